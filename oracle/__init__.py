@@ -1,0 +1,158 @@
+"""FP64 CPU oracle for the smeared PSF (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  The CUDA
+library never imports, links or calls it, and it never calls the library.
+
+The arithmetic lives in ``psf_oracle.c`` (plain loops, double precision,
+OpenMP over independent outputs); this module only compiles it with gcc and
+marshals numpy arrays through ctypes.  ``brute.py`` holds a second, undivided
+evaluation in extended precision used to pin the factored form.
+
+Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
+(closed forms, limits, symmetries, brute force, finite differences).  The
+accuracy levels the paper reads off its MeerKAT figures (Sect. 4, Figs. 4-7)
+are *parity unpinned*: they need the paper's array, dataset and imager.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "psf_oracle.c")
+_SO = os.path.join(_HERE, "_psf_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+EXACT, UV, IMG = 0, 1, 2
+WTERM, LITERAL_THETA = 1, 2
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared object (gcc, OpenMP, no fast-math)."""
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            obs_args = [ctypes.c_int] * 4 + [P] * 6
+            lib.or_nvis.restype = ctypes.c_int64
+            lib.or_nvis.argtypes = [ctypes.c_int] * 4 + [P]
+            lib.or_vis_table.restype = ctypes.c_int
+            lib.or_vis_table.argtypes = obs_args + [P]
+            lib.or_decorr.restype = ctypes.c_int
+            lib.or_decorr.argtypes = obs_args + [ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                 ctypes.c_int, P, P, P]
+            lib.or_psf.restype = ctypes.c_int
+            lib.or_psf.argtypes = obs_args + [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
+                                              ctypes.c_int, P, P, ctypes.c_int64, P]
+            lib.or_vjp.restype = ctypes.c_int
+            lib.or_vjp.argtypes = obs_args + [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
+                                              ctypes.c_int, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else ctypes.c_void_p(a.ctypes.data)
+
+
+class _Obs:
+    """Contiguous copies of an obsgen.Observation kept alive for a call."""
+
+    def __init__(self, obs):
+        self.uvw = np.ascontiguousarray(obs.uvw_m, np.float64)
+        self.t = np.ascontiguousarray(obs.time_s, np.float64)
+        self.f = np.ascontiguousarray(obs.freq_hz, np.float64)
+        self.w = np.ascontiguousarray(obs.chan_width_hz, np.float64)
+        self.tavg = np.ascontiguousarray(obs.tavg, np.int32)
+        self.wt = None if obs.weights is None else np.ascontiguousarray(obs.weights, np.float32)
+        self.nbl, self.ntime = self.uvw.shape[0], self.uvw.shape[1]
+        self.nchan, self.favg = self.f.shape[0], int(obs.favg)
+
+    def args(self):
+        return [self.nbl, self.ntime, self.nchan, self.favg, _p(self.uvw), _p(self.t),
+                _p(self.f), _p(self.w), _p(self.tavg), _p(self.wt)]
+
+
+def nvis(obs) -> int:
+    o = _Obs(obs)
+    return int(_load().or_nvis(o.nbl, o.ntime, o.nchan, o.favg, _p(o.tavg)))
+
+
+def vis_table(obs) -> dict:
+    """Per averaged visibility: u,v,w [lambda], nu, dnu, dt, W, ubar [m], dedge [m]."""
+    o = _Obs(obs)
+    n = nvis(obs)
+    out = np.empty((n, 13), np.float64)
+    if _load().or_vis_table(*o.args(), _p(out)) != 0:
+        raise ValueError("invalid observation")
+    return dict(uvw_lambda=out[:, 0:3], nu=out[:, 3], dnu=out[:, 4], dt=out[:, 5], W=out[:, 6],
+                ubar_m=out[:, 7:10], dedge_m=out[:, 10:13])
+
+
+def decorr(obs, method: int, l0: float, m0: float, flags: int = 0, grad: bool = False):
+    """D_k(l0, m0) as complex128 [nvis]; with grad, also dD [nvis, 4] (re/im d/dl0, d/dm0)."""
+    o = _Obs(obs)
+    n = nvis(obs)
+    dre = np.empty(n)
+    dim = np.empty(n)
+    dd = np.empty((n, 4)) if grad else None
+    if _load().or_decorr(*o.args(), int(method), float(l0), float(m0), int(flags),
+                         _p(dre), _p(dim), _p(dd)) != 0:
+        raise ValueError("invalid observation")
+    D = dre + 1j * dim
+    return (D, dd) if grad else D
+
+
+def _batch_arrays(batch, offsets=None):
+    lm = np.ascontiguousarray(batch.lm, np.float64)
+    npix = np.ascontiguousarray(batch.npix, np.int32)
+    if offsets is None:
+        n2 = npix.astype(np.int64) ** 2
+        offsets = np.concatenate([[0], np.cumsum(n2)[:-1]]).astype(np.int64)
+    offsets = np.ascontiguousarray(offsets, np.int64)
+    total = int((offsets + npix.astype(np.int64) ** 2).max()) if len(npix) else 0
+    return lm, npix, offsets, total
+
+
+def psf(obs, method: int, batch, flags: int = 0, pix_sel=None, offsets=None) -> np.ndarray:
+    """Packed cutouts (float64).  With pix_sel, only those packed indices are filled (rest NaN)."""
+    o = _Obs(obs)
+    lm, npix, offs, total = _batch_arrays(batch, offsets)
+    out = np.full(total, np.nan)
+    sel = None if pix_sel is None else np.ascontiguousarray(pix_sel, np.int64)
+    rc = _load().or_psf(*o.args(), int(method), lm.shape[0], _p(lm), _p(npix), float(batch.cell_rad),
+                        int(flags), _p(offs), _p(out), 0 if sel is None else sel.size, _p(sel))
+    if rc != 0:
+        raise ValueError("invalid observation")
+    return out
+
+
+def vjp(obs, method: int, batch, R: np.ndarray, flags: int = 0, offsets=None):
+    """(g_lm [npos,2], g_W [nvis]) for cotangent R in the packed output layout."""
+    o = _Obs(obs)
+    lm, npix, offs, total = _batch_arrays(batch, offsets)
+    R = np.ascontiguousarray(R, np.float64)
+    assert R.size >= total
+    g_lm = np.empty((lm.shape[0], 2))
+    g_W = np.empty(nvis(obs))
+    rc = _load().or_vjp(*o.args(), int(method), lm.shape[0], _p(lm), _p(npix), float(batch.cell_rad),
+                        int(flags), _p(offs), _p(R), _p(g_lm), _p(g_W))
+    if rc != 0:
+        raise ValueError("invalid observation")
+    return g_lm, g_W
