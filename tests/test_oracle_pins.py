@@ -277,3 +277,21 @@ def test_vis_table_bins_and_edges():
     np.testing.assert_allclose(tab["dnu"][:2], [4e6, 4e6])
     np.testing.assert_allclose(tab["dt"][0], 3 * 2.0)
     np.testing.assert_allclose(tab["uvw_lambda"][0], u[0:3].mean(0) * tab["nu"][0] / C, rtol=1e-15)
+
+
+def test_p3_unequal_contiguous_channels():
+    """Eq. 13 weights each raw channel by its width: channels of unequal widths that
+    tile a band average to the band integral, whose closed form is
+    exp(-2 pi i (nu_mid - nu_r) X / c) sinc_pi(X Dnu / c) after removing the
+    centre-visibility phase (nu_r is the mean of the channel centres)."""
+    widths = np.array([1e6, 3e6, 2e6])
+    edges = 1.2e9 + np.concatenate([[0], np.cumsum(widths)])
+    freq = 0.5 * (edges[:-1] + edges[1:])
+    obs = obsgen.linear_track_obs(2500.0, 0.0, ntime=1, dt=1.0, tavg=1,
+                                  freq_hz=freq, width_hz=widths, favg=3)
+    nu_r, nu_mid, dnu = freq.mean(), 0.5 * (edges[0] + edges[-1]), widths.sum()
+    for l0 in [0.004, 0.03]:
+        X = 2500.0 * l0
+        ref = np.exp(-2j * np.pi * (nu_mid - nu_r) * X / C) * np.sinc(X * dnu / C)
+        D = oracle.decorr(obs, oracle.EXACT, l0, 0.0)[0]
+        assert abs(D - ref) < 1e-12
