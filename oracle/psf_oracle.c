@@ -67,10 +67,15 @@ static double or_sincpi(double y) {
     return sin(OR_PI * y) / (OR_PI * y);
 }
 
-/* d/dy sinc_pi(y) = (cos(pi y) - sinc_pi(y)) / y, 0 at y = 0 */
+/* d/dy sinc_pi(y) = (cos(pi y) - sinc_pi(y)) / y.  For |pi y| < 0.05 the two terms
+ * cancel; there the Taylor series of d/dx (sin x / x), x = pi y, is used. */
 static double or_dsincpi(double y) {
-    if (fabs(y) < 1e-8) return -OR_PI * OR_PI * y / 3.0;
-    return (cos(OR_PI * y) - or_sincpi(y)) / y;
+    double x = OR_PI * y;
+    if (fabs(x) < 0.05) {
+        double x2 = x * x;
+        return OR_PI * x * (-1.0 / 3.0 + x2 * (1.0 / 30.0 + x2 * (-1.0 / 840.0 + x2 * (1.0 / 45360.0))));
+    }
+    return (cos(x) - sin(x) / x) / y;
 }
 
 static double or_dt(const or_obs *o) {
