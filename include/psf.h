@@ -1,0 +1,190 @@
+/*
+ * psf.h - C ABI of the GB300 (sm_103a) smeared-PSF library.
+ *
+ * The library evaluates the averaging-distorted ("smeared") point spread function
+ * of a radio interferometer at many sky positions (l0, m0), and the two fast
+ * approximations to it, as defined in Atemkeng, Smirnov, Tasse, Foster &
+ * Makhathini (2020), arXiv:2009.07010:
+ *
+ *   P_d(l0, l0 + dl) = sum_k W_k Re( D_k(l0) exp(2 pi i u_k . dl) )     (Eqs. 21-22)
+ *
+ * where k runs over averaged visibilities (baseline p<q, time bin, output
+ * channel), u_k is the bin-centre baseline in wavelengths (Sect. 2.1, Eq. 12),
+ * W_k the visibility weight (Eq. 6) and D_k the decorrelation of the bin:
+ *   exact      D_k = mean over the bin of the source fringe, with the
+ *                    centre-visibility phase removed (Eq. 13, boxcar Eq. 14)
+ *   approx_uv  D_k = sinc(dPsi/2) sinc(dPhi/2) from the baseline's uvw change
+ *                    across the bin and the channel width (Method 1, Eqs. 31-35)
+ *   approx_img D_k = the same sinc product from the circular-track model of
+ *                    Eqs. 38-44 / Algorithm 1 (Method 2), taken at the
+ *                    visibility's own uv point.
+ * Each cutout is the separable complex contraction A diag(w) B^T of per-visibility
+ * row twiddles exp(2 pi i u_k dl_i) and column twiddles exp(2 pi i v_k dm_j).
+ *
+ * Conventions: a source at l0 has visibility exp(-2 pi i u.l0) and imaging uses
+ * exp(+2 pi i u.l) (Eq. 1).  sinc(x) = sin(x)/x of the half phase change.  The sum
+ * runs over the supplied baselines only (p<q, no Hermitian conjugates), so at zero
+ * smearing the cutout peak equals sum_k W_k.  Cutout pixel (i, j) of an N x N
+ * cutout (N even) sits at (l0 + (i - N/2) cell, m0 + (j - N/2) cell) and is stored
+ * at out[offset + j*N + i] (row j = m offset, column i = l offset).
+ *
+ * Threading / streams: every compute call is asynchronous on the CUDA stream
+ * passed as `cuda_stream` (a cudaStream_t, NULL = legacy default stream).  Host
+ * inputs are consumed before the call returns.  A plan holds per-call scratch and
+ * must be used from one stream at a time.  Device pointers are plain device
+ * addresses on the current device.  No call throws; all return a status code.
+ */
+#ifndef PSF_GB300_PSF_H
+#define PSF_GB300_PSF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PSF_OK            0
+#define PSF_EINVAL       -1   /* bad argument: NULL, size, layout, odd N ... */
+#define PSF_ENOMEM       -2   /* host or device allocation failed            */
+#define PSF_ECUDA        -3   /* a CUDA runtime call failed (no device, ...) */
+#define PSF_EUNSUPPORTED -4   /* valid request outside what a path supports  */
+#define PSF_ETIMEOUT     -5   /* a bounded device-side wait gave up          */
+
+/* ---- precision of the contraction -------------------------------------- */
+#define PSF_FP32     0   /* FP32 CUDA-core form: weights, twiddles, sums in FP32   */
+#define PSF_TC_FP16  1   /* tcgen05 tensor cores, FP16 operands, FP32 accumulate  */
+#define PSF_TC_BF16  3   /* tcgen05 tensor cores, BF16 operands, FP32 accumulate  */
+
+/* ---- option flags ------------------------------------------------------ */
+#define PSF_WTERM             1u  /* use L0 = (l0, m0, n0-1): w enters the smearing */
+#define PSF_IMG_LITERAL_THETA 2u  /* Method 2 with theta = arctan(u/v) as printed   */
+
+/* ---- contraction algorithm (psf_opts_t.algo) ---------------------------- */
+#define PSF_ALGO_AUTO 0   /* per-cutout form for small batches, batched otherwise */
+#define PSF_ALGO_CUTOUT 1 /* per-cutout separable form, split over visibilities  */
+
+/* ---- methods (psf_adjoint) ---------------------------------------------- */
+#define PSF_METHOD_EXACT 0
+#define PSF_METHOD_UV    1
+#define PSF_METHOD_IMG   2
+
+typedef struct psf_plan_s *psf_plan_t;
+
+/* Raw observation (Sect. 2.1 and Eq. 12).  All arrays are host memory, owned by
+ * the caller, read during psf_plan only.
+ *   uvw_m          [nbl][ntime][3] float64, baseline q-p in metres, row-major
+ *   time_s         [ntime] raw sample centres, uniformly spaced (dt = spacing)
+ *   freq_hz        [nchan] raw channel centres
+ *   chan_width_hz  [nchan] raw channel widths
+ *   tavg           [nbl] raw samples averaged per time bin of each baseline
+ *                  (baseline-dependent averaging); a trailing partial bin is dropped
+ *   favg           raw channels per output channel; nchan % favg == 0
+ *   weights        [nvis] float32 visibility weights W_k in plan order, or NULL
+ *                  for natural weights W_k = tavg[b] * favg
+ * Plan order of averaged visibilities: baseline, then time bin, then output
+ * channel (innermost): k = (bin_index(b, tau)) * (nchan / favg) + r. */
+typedef struct {
+    int32_t nbl, ntime, nchan;
+    const double *uvw_m;
+    const double *time_s;
+    const double *freq_hz;
+    const double *chan_width_hz;
+    const int32_t *tavg;
+    int32_t favg;
+    const float *weights;
+} psf_obs_t;
+
+/* prec: PSF_FP32 / PSF_TC_FP16 / PSF_TC_BF16.  flags: PSF_WTERM |
+ * PSF_IMG_LITERAL_THETA.  algo: PSF_ALGO_*. */
+typedef struct {
+    int32_t prec;
+    uint32_t flags;
+    int32_t algo;
+    int32_t reserved;
+} psf_opts_t;
+
+/* A batch of cutout requests (positions l0 of Eq. 4, geometry of Algorithm 1).
+ *   npos        number of positions (0 is valid and does nothing)
+ *   lm          [npos][2] float64 direction cosines (l0, m0), host, l0^2+m0^2 < 1
+ *   npix        [npos] even cutout sizes N (2 <= N <= 4096), host, or NULL
+ *   npix0       size used for every position when npix is NULL
+ *   cell_rad    pixel size dl = dm (direction-cosine units), > 0
+ *   out_offset  [npos] float offsets of each cutout in the output, host, or NULL
+ *               for packed prefix sums of N^2; cutouts must not overlap */
+typedef struct {
+    int32_t npos;
+    const double *lm;
+    const int32_t *npix;
+    int32_t npix0;
+    double cell_rad;
+    const int64_t *out_offset;
+} psf_batch_t;
+
+/* Build a plan: bins raw samples (Eq. 12), forms bin centres and bin-edge deltas
+ * (Eqs. 31-33) in float64 on the host, rounds them to float32 and copies them to
+ * the current device.  Position independent; done once per observation.
+ * Returns PSF_EINVAL for inconsistent sizes/NULL arrays/non-uniform time steps,
+ * PSF_ENOMEM / PSF_ECUDA on allocation or copy failure.  *out is set on success
+ * and must be released with psf_plan_destroy. */
+int psf_plan(const psf_obs_t *obs, const psf_opts_t *opts, psf_plan_t *out);
+
+/* Replace the precision / flags / algorithm used by later calls on this plan. */
+int psf_plan_set_opts(psf_plan_t plan, const psf_opts_t *opts);
+
+/* Number of averaged visibilities K of the plan (-1 for a NULL plan). */
+int64_t psf_plan_nvis(psf_plan_t plan);
+
+/* Exact smeared PSF cutouts (Eqs. 13, 21-22).  out_dev: device float32 buffer
+ * of at least max(offset_p + N_p^2) floats, fully overwritten on the cutouts'
+ * pixels.  PSF_EUNSUPPORTED if a tensor-core precision is requested for N > 256. */
+int psf_exact(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
+
+/* Method 1, uv-plane approximation (Eqs. 31-35); same arguments as psf_exact. */
+int psf_approx_uv(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
+
+/* Method 2, image-plane approximation (Eqs. 38-44, Algorithm 1 at each
+ * visibility's uv point); same arguments as psf_exact. */
+int psf_approx_img(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
+
+/* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
+ * adjoint: given dL/dP (device float32, same layout as the forward output) it
+ * writes dL/d(l0,m0) to dL_dlm_dev (device float64 [npos][2], overwritten) and,
+ * if dL_dW_dev is not NULL, dL/dW_k summed over positions (device float32 [nvis],
+ * overwritten).  The position enters only through D_k (the twiddles depend on the
+ * pixel offsets only).  Always evaluated in FP32. */
+int psf_adjoint(psf_plan_t plan, int method, const psf_batch_t *batch, const float *dL_dP_dev,
+                double *dL_dlm_dev, float *dL_dW_dev, void *cuda_stream);
+
+/* Wait for the stream and report device-side failures of earlier calls on this
+ * plan: PSF_ETIMEOUT if a bounded wait inside a kernel gave up (the output of
+ * that call is then invalid), PSF_ECUDA if the stream reported an error. */
+int psf_sync_status(psf_plan_t plan, void *cuda_stream);
+
+/* Diagnostic timing.  With enable != 0, later compute calls on this plan record
+ * CUDA events on the caller's stream around every contraction-kernel launch (the
+ * dominant kernel of each call) and count the library's kernel launches.
+ * psf_profile_read waits for the recorded events and returns, since the previous
+ * read: the summed contraction time in milliseconds, the number of contraction
+ * launches and the number of kernel launches of any kind; then it resets.  Any
+ * output pointer may be NULL. */
+int psf_profile_enable(psf_plan_t plan, int enable);
+int psf_profile_read(psf_plan_t plan, double *contraction_ms, int64_t *contraction_launches,
+                     int64_t *kernel_launches);
+
+/* Release the plan and its device memory (NULL is ignored). */
+void psf_plan_destroy(psf_plan_t plan);
+
+/* Static text for a status code. */
+const char *psf_strerror(int status);
+
+/* Diagnostic: one 128 x n x 64 tcgen05 GEMM through the library's shared-memory
+ * operand layout and descriptors, D[m][j] = sum_k A[m][k] B[j][k] with FP16
+ * operands (a_dev [128][64], b_dev [n][64], row-major, device) and FP32 result
+ * d_dev [128][n] (device).  n in {16, 32, ..., 256}.  Synchronous. */
+int psf_selftest_umma(const void *a_dev, const void *b_dev, float *d_dev, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,165 @@
+"""Python binding of the smeared-PSF library (argument marshalling only).
+
+Every step of the computation runs in the CUDA library behind the C ABI of
+include/psf.h.  PyTorch provides device memory and the current CUDA stream; host
+inputs are numpy arrays.  Names follow the paper: l0, m0 positions, W_k weights,
+cell = pixel size, N = cutout size.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check
+
+PREC = {"fp32": _lib.PSF_FP32, "tc_fp16": _lib.PSF_TC_FP16, "tc_bf16": _lib.PSF_TC_BF16}
+METHODS = {"exact": _lib.EXACT, "uv": _lib.UV, "img": _lib.IMG}
+
+
+def _ptr(a: np.ndarray):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Batch:
+    """Host-side cutout requests marshalled into psf_batch_t."""
+
+    def __init__(self, lm, npix, cell_rad: float, out_offset=None):
+        self.lm = np.ascontiguousarray(np.asarray(lm, np.float64).reshape(-1, 2))
+        npos = self.lm.shape[0]
+        self.npix = np.ascontiguousarray(np.broadcast_to(np.asarray(npix, np.int32), (npos,)))
+        self.cell = float(cell_rad)
+        if out_offset is None:
+            n2 = self.npix.astype(np.int64) ** 2
+            self.offsets = np.concatenate([[0], np.cumsum(n2)[:-1]]).astype(np.int64) if npos else \
+                np.zeros(0, np.int64)
+            self._given = None
+        else:
+            self.offsets = np.ascontiguousarray(np.asarray(out_offset, np.int64))
+            self._given = self.offsets
+        self.npos = npos
+
+    @classmethod
+    def from_obsgen(cls, b):
+        return cls(b.lm, b.npix, b.cell_rad)
+
+    def total(self) -> int:
+        if self.npos == 0:
+            return 0
+        return int((self.offsets + self.npix.astype(np.int64) ** 2).max())
+
+    def struct(self) -> _lib.BatchT:
+        return _lib.BatchT(self.npos, self.lm.ctypes.data if self.npos else None,
+                           self.npix.ctypes.data if self.npos else None, 0, self.cell,
+                           None if self._given is None else self._given.ctypes.data)
+
+
+class Plan:
+    """A plan of one observation (psf_plan); owns device arrays until close()."""
+
+    def __init__(self, obs, prec: str = "fp32", flags: int = 0, algo: int = 0):
+        L = _lib.lib()
+        self._keep = [np.ascontiguousarray(obs.uvw_m, np.float64), np.ascontiguousarray(obs.time_s, np.float64),
+                      np.ascontiguousarray(obs.freq_hz, np.float64),
+                      np.ascontiguousarray(obs.chan_width_hz, np.float64),
+                      np.ascontiguousarray(obs.tavg, np.int32)]
+        wt = None if obs.weights is None else np.ascontiguousarray(obs.weights, np.float32)
+        uvw, t, f, w, tavg = self._keep
+        o = _lib.ObsT(uvw.shape[0], uvw.shape[1], f.shape[0], uvw.ctypes.data, t.ctypes.data, f.ctypes.data,
+                      w.ctypes.data, tavg.ctypes.data, int(obs.favg), None if wt is None else wt.ctypes.data)
+        opts = _lib.OptsT(PREC[prec], flags, algo, 0)
+        h = ctypes.c_void_p()
+        check(L.psf_plan(ctypes.byref(o), ctypes.byref(opts), ctypes.byref(h)), "psf_plan")
+        self._h = h
+        self._keep = None
+        self.prec, self.flags, self.algo = prec, flags, algo
+        self.nvis = int(L.psf_plan_nvis(h))
+
+    def set_opts(self, prec: Optional[str] = None, flags: Optional[int] = None, algo: Optional[int] = None):
+        self.prec = prec if prec is not None else self.prec
+        self.flags = flags if flags is not None else self.flags
+        self.algo = algo if algo is not None else self.algo
+        opts = _lib.OptsT(PREC[self.prec], self.flags, self.algo, 0)
+        check(_lib.lib().psf_plan_set_opts(self._h, ctypes.byref(opts)), "psf_plan_set_opts")
+
+    def forward(self, method: str, batch: Batch, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Cutouts of `method` ('exact' | 'uv' | 'img') into a device float32 tensor."""
+        if out is None:
+            out = torch.empty(max(batch.total(), 1), dtype=torch.float32, device="cuda")
+        assert out.dtype == torch.float32 and out.is_cuda and out.is_contiguous()
+        assert out.numel() >= batch.total()
+        fn = {"exact": "psf_exact", "uv": "psf_approx_uv", "img": "psf_approx_img"}[method]
+        bs = batch.struct()
+        check(getattr(_lib.lib(), fn)(self._h, ctypes.byref(bs), ctypes.c_void_p(out.data_ptr()),
+                                      _stream_handle(stream)), fn)
+        return out
+
+    def exact(self, batch, out=None, stream=None):
+        return self.forward("exact", batch, out, stream)
+
+    def approx_uv(self, batch, out=None, stream=None):
+        return self.forward("uv", batch, out, stream)
+
+    def approx_img(self, batch, out=None, stream=None):
+        return self.forward("img", batch, out, stream)
+
+    def adjoint(self, method: str, batch: Batch, dL_dP: torch.Tensor, want_dW: bool = True, stream=None):
+        """(dL/d(l0,m0) float64 [npos,2], dL/dW float32 [nvis] or None) on the device."""
+        assert dL_dP.dtype == torch.float32 and dL_dP.is_cuda and dL_dP.is_contiguous()
+        g_lm = torch.empty((max(batch.npos, 1), 2), dtype=torch.float64, device="cuda")
+        g_W = torch.empty(self.nvis, dtype=torch.float32, device="cuda") if want_dW else None
+        bs = batch.struct()
+        check(_lib.lib().psf_adjoint(self._h, METHODS[method], ctypes.byref(bs), ctypes.c_void_p(dL_dP.data_ptr()),
+                                     ctypes.c_void_p(g_lm.data_ptr()),
+                                     None if g_W is None else ctypes.c_void_p(g_W.data_ptr()),
+                                     _stream_handle(stream)), "psf_adjoint")
+        return g_lm[:batch.npos], g_W
+
+    def profile_enable(self, enable: bool = True):
+        check(_lib.lib().psf_profile_enable(self._h, 1 if enable else 0), "psf_profile_enable")
+
+    def profile_read(self):
+        """(contraction ms, contraction launches, kernel launches) since the last read."""
+        ms, nc, nk = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+        check(_lib.lib().psf_profile_read(self._h, ctypes.byref(ms), ctypes.byref(nc), ctypes.byref(nk)),
+              "psf_profile_read")
+        return ms.value, nc.value, nk.value
+
+    def sync_status(self, stream=None) -> int:
+        return int(_lib.lib().psf_sync_status(self._h, _stream_handle(stream)))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.lib().psf_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def selftest_umma(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """D = A B^T through one tcgen05 MMA tile (A [128,64] fp16, B [n,64] fp16)."""
+    assert a.shape == (128, 64) and a.dtype == torch.float16 and b.dtype == torch.float16 and b.shape[1] == 64
+    a, b = a.contiguous(), b.contiguous()
+    d = torch.empty((128, b.shape[0]), dtype=torch.float32, device="cuda")
+    check(_lib.lib().psf_selftest_umma(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                       ctypes.c_void_p(d.data_ptr()), b.shape[0]), "psf_selftest_umma")
+    return d

@@ -1,0 +1,201 @@
+// Per-visibility decorrelation D_k(l0) on the device (float32), and its gradient.
+//
+// All phases are formed difference-first: the centre-visibility phase u_k . L0
+// (thousands of turns) cancels analytically against the cutout centring, so only
+// small quantities (sample offsets from the bin mean, channel offsets from the
+// bin centre, sinc arguments) are ever evaluated.  sinpif / sincospif are CUDA's
+// own functions; sinc, the Dirichlet kernel and their derivatives are written out
+// from their definitions here.
+#pragma once
+
+#include "psf_internal.cuh"
+
+namespace psf {
+
+constexpr float kInvC = (float)(1.0 / kCLight);
+constexpr float kPiF = 3.14159265358979f;
+
+// sinc_pi(y) = sin(pi y) / (pi y), 1 at y = 0.
+__device__ __forceinline__ float sincpi(float y) {
+    return y == 0.0f ? 1.0f : sinpif(y) / (kPiF * y);
+}
+
+// d/dy sinc_pi(y) = (cos(pi y) - sinc_pi(y)) / y.  Below |pi y| = 1/2 the two
+// terms cancel, so the Taylor series of d/dx (sin x / x) at x = pi y is used.
+__device__ __forceinline__ float dsincpi(float y) {
+    const float x = kPiF * y;
+    if (fabsf(x) < 0.5f) {
+        const float x2 = x * x;
+        return kPiF * x * (-1.0f / 3.0f + x2 * (1.0f / 30.0f + x2 * (-1.0f / 840.0f + x2 * (1.0f / 45360.0f))));
+    }
+    float s, c;
+    sincospif(y, &s, &c);
+    return (c - s / x) / y;
+}
+
+// Mean of exp(-2 pi i (c - (F-1)/2) a) over c = 0..F-1, i.e. the Dirichlet kernel
+// sin(pi F a) / (F sin(pi a)).  a is split as n + r with |r| <= 1/2 so the ratio
+// is taken between two small sines: sin(pi F (n+r)) = (-1)^(F n) sin(pi F r).
+__device__ __forceinline__ float dirichlet(int F, float a) {
+    if (F == 1) return 1.0f;
+    float n = rintf(a);
+    float r = a - n;
+    float sgn = (((int)n * (F - 1)) & 1) ? -1.0f : 1.0f;
+    if (r == 0.0f) return sgn;
+    return sgn * sinpif((float)F * r) / ((float)F * sinpif(r));
+}
+
+// d/da of the Dirichlet kernel above.  With x = pi r the numerator
+// F cos(F x) sin(x) - sin(F x) cos(x) cancels to O((F x)^3) for small F x; there
+// the series 1 - (F^2-1) x^2 / 6 + (7/360 - F^2/36 + F^4/120) x^4 is differentiated.
+__device__ __forceinline__ float ddirichlet(int F, float a) {
+    if (F == 1) return 0.0f;
+    float n = rintf(a);
+    float r = a - n;
+    float sgn = (((int)n * (F - 1)) & 1) ? -1.0f : 1.0f;
+    const float Ff = (float)F, F2 = Ff * Ff;
+    const float x = kPiF * r;
+    if (fabsf(Ff * x) < 0.05f) {
+        const float c4 = 7.0f / 360.0f - F2 / 36.0f + F2 * F2 / 120.0f;
+        return sgn * kPiF * (x * (1.0f - F2) / 3.0f + 4.0f * c4 * x * x * x);
+    }
+    float sF, cF, s1, c1;
+    sincospif(Ff * r, &sF, &cF);
+    sincospif(r, &s1, &c1);
+    return sgn * kPiF * (Ff * cF * s1 - sF * c1) / (Ff * s1 * s1);
+}
+
+__device__ __forceinline__ float dot3(float4 a, float4 L) { return a.x * L.x + a.y * L.y + a.z * L.z; }
+
+// Exact bin average (Eq. 13), centre phase removed.  With uniform channels the
+// channel sum is the Dirichlet kernel times the per-channel sinc (exact identity
+// for equally spaced, equally wide channels); otherwise channels are summed.
+// grad (optional): d/dl0 (re, im), d/dm0 (re, im) with dL0/dl0 = dLl, dL0/dm0 = dLm.
+template <bool GRAD>
+__device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, float4 L, float4 dLl,
+                                               float4 dLm, float4 *grad) {
+    const float4 ub = o.bin_ubar[bin];
+    const int2 sm = o.bin_samp[bin];
+    const float4 ch = o.chan[r];
+    const float Xbar = dot3(ub, L);
+    float re = 0.f, im = 0.f, glr = 0.f, gli = 0.f, gmr = 0.f, gmi = 0.f;
+    float Xbl = 0.f, Xbm = 0.f;
+    if (GRAD) { Xbl = dot3(ub, dLl); Xbm = dot3(ub, dLm); }
+    for (int s = 0; s < sm.y; ++s) {
+        const float4 d = o.samp[sm.x + s];
+        const float ds = dot3(d, L);
+        const float Xs = Xbar + ds;
+        // exp(-2 pi i nu_r ds / c): the sample's offset from the bin centre
+        float sn, cs;
+        sincospif(-2.0f * ch.x * ds * kInvC, &sn, &cs);
+        float dsl = 0.f, dsm = 0.f;
+        if (GRAD) { dsl = dot3(d, dLl); dsm = dot3(d, dLm); }
+        if (o.uniform) {
+            const float a = ch.z * Xs * kInvC;
+            const float y = ch.w * Xs * kInvC;
+            const float dir = dirichlet(o.favg, a);
+            const float sc = sincpi(y);
+            const float f = dir * sc;
+            re += cs * f;
+            im += sn * f;
+            if (GRAD) {
+                const float df = (ddirichlet(o.favg, a) * ch.z * sc + dir * dsincpi(y) * ch.w) * kInvC;
+                const float Xl = Xbl + dsl, Xm = Xbm + dsm;
+                const float pl = -2.0f * kPiF * ch.x * dsl * kInvC;   // d(phase)/dl0 [rad]
+                const float pm = -2.0f * kPiF * ch.x * dsm * kInvC;
+                // d[(cs + i sn) f] = (cs + i sn)(i dphase f + df dX)
+                glr += cs * df * Xl - sn * pl * f;
+                gli += sn * df * Xl + cs * pl * f;
+                gmr += cs * df * Xm - sn * pm * f;
+                gmi += sn * df * Xm + cs * pm * f;
+            }
+        } else {
+            for (int c = 0; c < o.favg; ++c) {
+                const float4 rc = o.rawchan[r * o.favg + c];
+                float s2, c2;
+                sincospif(-2.0f * rc.x * Xs * kInvC, &s2, &c2);
+                const float y = rc.y * Xs * kInvC;
+                const float S = sincpi(y) * rc.z;
+                const float er = cs * c2 - sn * s2, ei = cs * s2 + sn * c2;
+                re += er * S;
+                im += ei * S;
+                if (GRAD) {
+                    const float dS = dsincpi(y) * rc.y * kInvC * rc.z;
+                    const float Xl = Xbl + dsl, Xm = Xbm + dsm;
+                    const float pl = -2.0f * kPiF * (ch.x * dsl + rc.x * Xl) * kInvC;
+                    const float pm = -2.0f * kPiF * (ch.x * dsm + rc.x * Xm) * kInvC;
+                    glr += er * dS * Xl - ei * pl * S;
+                    gli += ei * dS * Xl + er * pl * S;
+                    gmr += er * dS * Xm - ei * pm * S;
+                    gmi += ei * dS * Xm + er * pm * S;
+                }
+            }
+        }
+    }
+    const float inv = 1.0f / (float)sm.y;
+    if (GRAD) *grad = make_float4(glr * inv, gli * inv, gmr * inv, gmi * inv);
+    return make_float2(re * inv, im * inv);
+}
+
+// Method 1 (Eqs. 31-35): sinc_pi(dedge.L0 nu_r / c) * sinc_pi(ubar.L0 Dnu_r / c).
+template <bool GRAD>
+__device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, float4 L, float4 dLl,
+                                            float4 dLm, float4 *grad) {
+    const float4 ub = o.bin_ubar[bin];
+    const float4 ed = o.bin_edge[bin];
+    const float4 ch = o.chan[r];
+    const float A = dot3(ed, L) * ch.x * kInvC;
+    const float B = dot3(ub, L) * ch.y * kInvC;
+    const float sA = sincpi(A), sB = sincpi(B);
+    if (GRAD) {
+        const float dA = dsincpi(A), dB = dsincpi(B);
+        const float Al = dot3(ed, dLl) * ch.x * kInvC, Am = dot3(ed, dLm) * ch.x * kInvC;
+        const float Bl = dot3(ub, dLl) * ch.y * kInvC, Bm = dot3(ub, dLm) * ch.y * kInvC;
+        *grad = make_float4(dA * Al * sB + sA * dB * Bl, 0.f, dA * Am * sB + sA * dB * Bm, 0.f);
+    }
+    return make_float2(sA * sB, 0.0f);
+}
+
+// Method 2 (Eqs. 38-44, Algorithm 1 at the visibility's own uv point):
+//   (du/dt, dv/dt) = omega_E (-v, u) for theta = atan2(v, u), or the literal
+//   arctan(u/v) reading when PSF_IMG_LITERAL_THETA is set;
+//   D = sinc_pi(omega_E Dt (udot l0 + vdot m0)) sinc_pi((Dnu/nu) |u| |l0|).
+template <bool GRAD>
+__device__ __forceinline__ float2 decorr_img(const DevObs &o, int bin, int r, float4 L,
+                                             uint32_t flags, float4 *grad) {
+    const float4 ub = o.bin_ubar[bin];
+    const float4 ch = o.chan[r];
+    const float s = ch.x * kInvC;
+    const float u = ub.x * s, v = ub.y * s;
+    const float uvlen = sqrtf(u * u + v * v);
+    float udot = -v, vdot = u;
+    if (flags & PSF_IMG_LITERAL_THETA) {
+        const float th = (v != 0.0f) ? atanf(u / v) : (u >= 0.0f ? 0.5f * kPiF : -0.5f * kPiF);
+        float st, ct;
+        sincosf(th, &st, &ct);
+        udot = -uvlen * st;
+        vdot = uvlen * ct;
+    }
+    const float wdt = (float)kOmegaE * ub.w;
+    const float rho = sqrtf(L.x * L.x + L.y * L.y);
+    const float fb = ch.y / ch.x * uvlen;
+    const float A = wdt * (udot * L.x + vdot * L.y);
+    const float B = fb * rho;
+    const float sA = sincpi(A), sB = sincpi(B);
+    if (GRAD) {
+        const float dA = dsincpi(A), dB = dsincpi(B);
+        const float Bl = rho > 0.f ? fb * L.x / rho : 0.f, Bm = rho > 0.f ? fb * L.y / rho : 0.f;
+        *grad = make_float4(dA * wdt * udot * sB + sA * dB * Bl, 0.f, dA * wdt * vdot * sB + sA * dB * Bm, 0.f);
+    }
+    return make_float2(sA * sB, 0.0f);
+}
+
+template <bool GRAD>
+__device__ __forceinline__ float2 decorr(const DevObs &o, int method, uint32_t flags, int bin, int r,
+                                         float4 L, float4 dLl, float4 dLm, float4 *grad) {
+    if (method == kExact) return decorr_exact<GRAD>(o, bin, r, L, dLl, dLm, grad);
+    if (method == kUV) return decorr_uv<GRAD>(o, bin, r, L, dLl, dLm, grad);
+    return decorr_img<GRAD>(o, bin, r, L, flags, grad);
+}
+
+}  // namespace psf

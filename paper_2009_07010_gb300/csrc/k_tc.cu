@@ -1,0 +1,469 @@
+// tcgen05 (5th-generation tensor core) contraction of the smeared PSF, sm_103a.
+//
+// One CTA computes one 128 x ncols output tile of one cutout over a contiguous
+// range of visibilities (split-K), as the real GEMM of Eqs. 21-22 in separable form:
+//   P[j][i] = sum_k Re( c_k[j] a_k[i] ),   c_k[j] = w_k exp(2 pi i v_k dm_j),
+//                                          a_k[i] = exp(2 pi i u_k dl_i),
+//   A'[j][2k] = Re c, A'[j][2k+1] = Im c,  B'[i][2k] = Re a, B'[i][2k+1] = -Im a,
+//   P = A' B'^T  with K' = 2K (FP16 or BF16 operands, FP32 accumulation in TMEM).
+//
+// Warp roles (416 threads):
+//   warps 0-7   operand generators: per pipeline stage of 32 visibilities each lane
+//               owns one visibility and walks a 32-row recurrence chain
+//               (seed and step from the MUFU sin/cos of the reduced phase, then
+//               complex multiplication), writing FP16/BF16 pairs straight into the
+//               128-byte-swizzled K-major shared-memory layout the MMA reads;
+//   warp 12     TMEM allocation and the single-thread tcgen05.mma issue loop;
+//   warps 8-11  drain: every kDrainStages stages the MMA switches to the second TMEM
+//               accumulator while these warps read the first (tcgen05.ld) and add it
+//               into the CTA's FP32 partial tile in global memory.  Short TMEM
+//               accumulation runs bound the tensor-core rounding growth.
+// Stages are handed over with mbarriers (generators -> MMA: `full`, MMA commit ->
+// generators: `empty`, MMA commit -> drain: `acc_full`, drain -> MMA: `acc_empty`).
+// Every wait is bounded by a wall-clock limit; on expiry the CTA raises the plan's
+// error flag, stops all roles, waits (bounded) for its issued MMAs and frees TMEM.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "psf_internal.cuh"
+
+namespace psf {
+namespace {
+
+constexpr int kStages = 4;
+constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
+constexpr int kGenWarps = 8;
+constexpr int kDrainWarp0 = 8;
+constexpr int kMmaWarp = 12;
+constexpr int kThreads = 13 * 32;
+constexpr int kDrainStages = 64;   // stages accumulated in TMEM between drains
+constexpr int kATileBytes = 128 * 128;
+constexpr unsigned long long kTimeoutNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait for the phase of `bar` with the given parity.  Returns false if the CTA is
+// aborting or the wall-clock limit expired (then the abort flag and the global
+// error flag are raised).
+__device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
+                                             int *err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((it & 255u) == 0) {
+            if (*abort_flag) return false;
+            if (globaltimer() - t0 > kTimeoutNs) {
+                *abort_flag = 1;
+                if (err) atomicExch(err, 1);
+                return false;
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t *dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, one CTA.
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Arrive on `bar` once all previously issued tcgen05.mma of this thread complete.
+__device__ __forceinline__ void umma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+
+// 32 TMEM lanes x 16 consecutive 32-bit columns -> 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    return (uint64_t)((saddr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Instruction descriptor, kind::f16: FP32 accumulator, FP16 (0) or BF16 (1)
+// operands, both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int bf16) {
+    return (1u << 4) | ((uint32_t)bf16 << 7) | ((uint32_t)bf16 << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+// Byte offset of the 32-bit (re, im) pair `kp` (0..31) of row `row` in a K-major
+// 128-byte-swizzled tile: 16-byte chunk index XOR (row mod 8).
+__device__ __forceinline__ uint32_t sw128_pair_offset(int row, int kp) {
+    return (uint32_t)row * 128u + ((uint32_t)(((kp >> 2) ^ (row & 7))) << 4) + ((uint32_t)(kp & 3) << 2);
+}
+
+template <int BF16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    if (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(lo, hi);
+        return *reinterpret_cast<uint32_t *>(&h);
+    }
+}
+
+__device__ __forceinline__ uint32_t pow2_cols(int n) {
+    uint32_t c = 32;
+    while ((int)c < n) c <<= 1;
+    return c;
+}
+
+// exp(2 pi i x) via the MUFU sine/cosine of the reduced argument (|error| ~ 1e-6).
+__device__ __forceinline__ float2 cis_turns(float x) {
+    const float f = x - rintf(x);
+    float s, c;
+    __sincosf(6.28318530717958647f * f, &s, &c);
+    return make_float2(c, s);
+}
+
+struct SmemLayout {
+    uint32_t a_off, b_off, bar_off, bytes;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int ncols_max) {
+    SmemLayout L;
+    const uint32_t bt = (uint32_t)ncols_max * 128u;
+    L.a_off = 0;
+    L.b_off = kStages * kATileBytes;
+    L.bar_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
+    L.bytes = L.bar_off + 256;
+    return L;
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
+             const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
+             int64_t split_stride, int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    // 1024-byte alignment of the operand tiles (swizzle atoms)
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const SmemLayout L = smem_layout(ncols_max);
+    uint64_t *full = (uint64_t *)(smem + L.bar_off);
+    uint64_t *empty = full + kStages;
+    uint64_t *acc_full = empty + kStages;
+    uint64_t *acc_empty = acc_full + 2;
+    uint64_t *done_bar = acc_empty + 2;
+    uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+
+    const TcItem it = items[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ncols = it.ncols;
+    const uint32_t bt_stride = ((uint32_t)ncols_max * 128u + 1023u) / 1024u * 1024u;
+    const uint32_t acc_cols = pow2_cols(ncols_max);
+    const int nst = (it.k1 - it.k0 + kKS - 1) / kKS;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], kGenWarps);
+            mbar_init(&empty[s], 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);
+        }
+        mbar_init(done_bar, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kMmaWarp) {
+        tmem_alloc(s_tmem, 2 * acc_cols);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    if (warp < kGenWarps) {
+        // ------------------------------------------------------------ generators
+        const int arows = 128, nA = 4, nB = (ncols + 31) / 32;
+        const int half = it.N / 2;
+        const float2 *wp = w + (int64_t)it.slot * ldw;
+        uint32_t off8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
+        for (int s_i = 0; s_i < nst; ++s_i) {
+            const int slot = s_i % kStages;
+            const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
+            if (s_i >= kStages) {
+                const bool ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
+                if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
+            }
+            const int32_t k = it.k0 + s_i * kKS + lane;
+            float2 uvk = make_float2(0.f, 0.f), wk = make_float2(0.f, 0.f);
+            if (k < it.k1) {
+                uvk = uv[k];
+                wk = wp[k];
+            }
+            uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
+            uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
+            for (int ch = warp; ch < nA + nB; ch += kGenWarps) {
+                const bool isA = ch < nA;
+                const int r0 = (isA ? ch : ch - nA) * 32;
+                const int rows = isA ? arows : ncols;
+                const float theta = (isA ? uvk.y : uvk.x) * cell;   // turns per pixel
+                const int n0 = (isA ? it.j0 : it.i0) + r0 - half;
+                float2 z = cis_turns(theta * (float)n0);
+                const float2 step = cis_turns(theta);
+                if (isA) z = make_float2(z.x * wk.x - z.y * wk.y, z.x * wk.y + z.y * wk.x);
+                const float sgn = isA ? 1.0f : -1.0f;
+                uint8_t *base = (isA ? a_tile : b_tile) + r0 * 128;
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    if (r0 + q < rows)
+                        *reinterpret_cast<uint32_t *>(base + q * 128 + off8[q & 7]) = pack2<BF16>(z.x, sgn * z.y);
+                    z = make_float2(z.x * step.x - z.y * step.y, z.x * step.y + z.y * step.x);
+                }
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[slot]);
+        }
+    } else if (warp == kMmaWarp) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, ncols, BF16);
+            int acc = 0, in_acc = 0;
+            int uses[2] = {0, 0};
+            const uint32_t a0 = smem_u32(smem + L.a_off), b0 = smem_u32(smem + L.b_off);
+            for (int s_i = 0; s_i < nst; ++s_i) {
+                const int slot = s_i % kStages;
+                const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
+                if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
+                if (in_acc == 0 && uses[acc] > 0 &&
+                    !wait_bounded(&acc_empty[acc], (uint32_t)(uses[acc] - 1) & 1u, s_abort, err))
+                    break;
+                tc_fence_after();
+                const uint64_t ad = desc_sw128(a0 + slot * kATileBytes);
+                const uint64_t bd = desc_sw128(b0 + slot * bt_stride);
+                const uint32_t dt = tmem + (uint32_t)acc * acc_cols;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)   // K' = 16 per MMA = 32 bytes of the 128-byte row
+                    umma_f16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
+                             (in_acc > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(&empty[slot]);
+                if (++in_acc == kDrainStages || s_i == nst - 1) {
+                    umma_commit(&acc_full[acc]);
+                    uses[acc]++;
+                    acc ^= 1;
+                    in_acc = 0;
+                }
+            }
+            // all issued MMAs complete before TMEM is released
+            umma_commit(done_bar);
+            wait_bounded(done_bar, 0, s_abort, nullptr);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ drain
+        const int q = warp - kDrainWarp0;          // TMEM lane quarter (warp % 4)
+        const int j = it.j0 + q * 32 + lane;       // output row (m offset index)
+        float *dst = partial + (int64_t)it.split * split_stride + it.out_off + (int64_t)j * it.N + it.i0;
+        const bool row_ok = j < it.N;
+        const int ncol_valid = min(ncols, it.N - it.i0);
+        if (nst == 0) {
+            if (row_ok)
+                for (int c = 0; c < ncol_valid; ++c) dst[c] = 0.f;
+        }
+        const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
+        for (int d = 0; d < ndrain; ++d) {
+            const int acc = d & 1;
+            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err);
+            if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
+            tc_fence_after();
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
+            for (int c0 = 0; c0 < ncols; c0 += 16) {
+                float v[16];
+                tmem_ld16(ta + (uint32_t)c0, v);
+                if (row_ok) {
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int c = c0 + e;
+                        if (c < ncol_valid) dst[c] = (d == 0) ? v[e] : dst[c] + v[e];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kMmaWarp) tmem_dealloc(tmem, 2 * acc_cols);
+}
+
+// Self-test: one 128 x n x 64 FP16 GEMM through the same layout, descriptors,
+// instruction descriptor and TMEM read-out as the contraction kernel.
+__global__ void __launch_bounds__(128, 1)
+    k_selftest(const __half *__restrict__ A, const __half *__restrict__ B, float *__restrict__ D, int n,
+               int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *a_tile = smem;
+    uint8_t *b_tile = smem + kATileBytes;
+    uint64_t *bar = (uint64_t *)(smem + kATileBytes + 256 * 128);
+    uint32_t *s_tmem = (uint32_t *)(bar + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t cols = pow2_cols(n);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        tmem_alloc(s_tmem, cols);
+        tmem_relinquish();
+    }
+    // operands: pairs of FP16 (k' = 2 kp, 2 kp + 1) into the swizzled K-major tiles
+    for (int idx = threadIdx.x; idx < 128 * 32; idx += blockDim.x) {
+        const int row = idx >> 5, kp = idx & 31;
+        *reinterpret_cast<uint32_t *>(a_tile + sw128_pair_offset(row, kp)) =
+            *reinterpret_cast<const uint32_t *>(A + row * 64 + 2 * kp);
+    }
+    for (int idx = threadIdx.x; idx < n * 32; idx += blockDim.x) {
+        const int row = idx >> 5, kp = idx & 31;
+        *reinterpret_cast<uint32_t *>(b_tile + sw128_pair_offset(row, kp)) =
+            *reinterpret_cast<const uint32_t *>(B + row * 64 + 2 * kp);
+    }
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+    if (threadIdx.x == 0) {
+        const uint32_t idesc = idesc_f16(128, n, 0);
+        const uint64_t ad = desc_sw128(smem_u32(a_tile)), bd = desc_sw128(smem_u32(b_tile));
+        for (int kk = 0; kk < 4; ++kk) umma_f16(tmem, ad + 2 * kk, bd + 2 * kk, idesc, kk > 0 ? 1u : 0u);
+        umma_commit(bar);
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, wait_bounded(bar, 0, s_abort, err));
+    tc_fence_after();
+    if (ok) {
+        const uint32_t ta = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < n; c0 += 16) {
+            float v[16];
+            tmem_ld16(ta + (uint32_t)c0, v);
+            for (int e = 0; e < 16; ++e) D[(warp * 32 + lane) * n + c0 + e] = v[e];
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, cols);
+}
+
+}  // namespace
+
+cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
+                          int ncols_max, int bf16, float cell, float *partial, int64_t split_stride, int *err,
+                          cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const SmemLayout L = smem_layout(ncols_max);
+    const size_t bytes = L.bytes + 1024;
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(k_psf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        k_psf_tc<1><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
+                                                     err);
+    } else {
+        e = cudaFuncSetAttribute(k_psf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+        if (e != cudaSuccess) return e;
+        k_psf_tc<0><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
+                                                     err);
+    }
+    return cudaGetLastError();
+}
+
+int selftest_umma(const void *a, const void *b, float *d, int n) {
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return PSF_ENOMEM; }
+    cudaMemset(err, 0, sizeof(int));
+    const size_t bytes = kATileBytes + 256 * 128 + 256 + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_selftest, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) {
+        k_selftest<<<1, 128, bytes>>>((const __half *)a, (const __half *)b, d, n, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) { cudaGetLastError(); return PSF_ECUDA; }
+    return flag ? PSF_ETIMEOUT : PSF_OK;
+}
+
+}  // namespace psf

@@ -1,0 +1,193 @@
+// Smearing weights w_{p,k} = W_k D_k(l0_p), the FP32 CUDA-core contraction and the
+// float64 reduction of split-K partial cutouts.
+//
+// Weights (Eqs. 13, 35, 44): one thread per (position, visibility), streamed over
+// visibilities with coalesced 16-byte loads of the bin records.
+//
+// FP32 contraction (Eqs. 21-22 as a separable DFT): a CTA owns a 64 x 64 pixel tile
+// of one cutout and a contiguous range of visibilities.  Per chunk of 32
+// visibilities it stages the row twiddles a_k[i] = exp(2 pi i u_k dl_i) and the
+// weighted column twiddles c_k[j] = w_k exp(2 pi i v_k dm_j) in shared memory
+// (generated by complex recurrence from sincospif seeds), then every thread
+// accumulates a 4 x 4 pixel block of Re(c a) with two FMAs per term.  Sums are
+// kept short in FP32 (one chunk) and folded into a compensated (Kahan) FP32 total,
+// and split-K partials are added in float64, so the path meets 1e-6 relative.
+#include "decorr.cuh"
+
+namespace psf {
+
+// --------------------------------------------------------------- weights
+__global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t flags,
+                                                 const float4 *__restrict__ pos, int32_t k0,
+                                                 int32_t kn, float2 *__restrict__ w, int64_t ldw) {
+    const int p = blockIdx.y;
+    const int32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= kn) return;
+    const int32_t k = k0 + kk;
+    const int bin = k / o.nout;
+    const int r = k - bin * o.nout;
+    const float4 L = pos[p];
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    float2 D = decorr<false>(o, method, flags, bin, r, L, z, z, nullptr);
+    const float Wk = o.W[k];
+    w[(int64_t)p * ldw + kk] = make_float2(Wk * D.x, Wk * D.y);
+}
+
+cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos, int npos,
+                           int32_t k0, int32_t kn, float2 *w, int64_t ldw, cudaStream_t st) {
+    if (npos <= 0 || kn <= 0) return cudaSuccess;
+    dim3 grid((kn + 255) / 256, npos);
+    k_weights<<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- FP32 contraction
+namespace {
+constexpr int kT = 64;    // tile edge (pixels)
+constexpr int kKC = 32;   // visibilities per shared-memory chunk
+constexpr int kSeg = 16;  // twiddles per recurrence chain
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_psf_fp32(const float2 *__restrict__ uv,
+                                                  const float2 *__restrict__ w, int64_t ldw,
+                                                  int32_t nvis, const Tile *__restrict__ tiles,
+                                                  int32_t kper, float cell, float *__restrict__ partial,
+                                                  int64_t split_stride) {
+    __shared__ __align__(16) float2 sa[kKC][kT];   // row (l) twiddles
+    __shared__ __align__(16) float2 sc[kKC][kT];   // weighted column (m) twiddles
+    const Tile t = tiles[blockIdx.x];
+    const int split = blockIdx.y;
+    const int32_t kbeg = split * kper;
+    const int32_t kend = min(nvis, kbeg + kper);
+    const float2 *wp = w + (int64_t)t.slot * ldw;
+    const int tid = threadIdx.x;
+    const int tx = tid & 15, ty = tid >> 4;
+    // generator role: visibility lane gk of the chunk, 16-twiddle segment gs (0-3 rows, 4-7 cols)
+    const int gk = tid & 31, gs = tid >> 5;
+    const int half = t.N / 2;
+    const int seg_first = (gs & 3) * kSeg;
+    const int n_first = (gs < 4 ? t.i0 : t.j0) + seg_first - half;   // pixel offset index of the chain start
+
+    float acc[4][4], tot[4][4], cmp[4][4];
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+#pragma unroll
+        for (int a = 0; a < 4; ++a) { acc[b][a] = 0.f; tot[b][a] = 0.f; cmp[b][a] = 0.f; }
+
+    for (int32_t kc = kbeg; kc < kend; kc += kKC) {
+        const int32_t k = kc + gk;
+        float2 seed = make_float2(0.f, 0.f), step = make_float2(1.f, 0.f);
+        if (k < kend) {
+            const float2 uvk = uv[k];
+            const float theta = (gs < 4 ? uvk.x : uvk.y) * cell;   // turns per pixel
+            sincospif(2.0f * theta * (float)n_first, &seed.y, &seed.x);
+            sincospif(2.0f * theta, &step.y, &step.x);
+            if (gs >= 4) seed = cmul(seed, wp[k]);
+        }
+        __syncthreads();   // previous chunk consumed
+        float2 *dst = (gs < 4 ? &sa[gk][seg_first] : &sc[gk][seg_first]);
+#pragma unroll
+        for (int q = 0; q < kSeg; ++q) {
+            dst[q] = seed;
+            seed = cmul(seed, step);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kKC; ++kk) {
+            const float4 a01 = *reinterpret_cast<const float4 *>(&sa[kk][tx * 4]);
+            const float4 a23 = *reinterpret_cast<const float4 *>(&sa[kk][tx * 4 + 2]);
+            const float4 c01 = *reinterpret_cast<const float4 *>(&sc[kk][ty * 4]);
+            const float4 c23 = *reinterpret_cast<const float4 *>(&sc[kk][ty * 4 + 2]);
+            const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
+            const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+#pragma unroll
+                for (int a = 0; a < 4; ++a) acc[b][a] = fmaf(cr[b], ar[a], fmaf(-ci[b], ai[a], acc[b][a]));
+        }
+        // fold the chunk sum into the compensated total
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const float y = acc[b][a] - cmp[b][a];
+                const float s = tot[b][a] + y;
+                cmp[b][a] = (s - tot[b][a]) - y;
+                tot[b][a] = s;
+                acc[b][a] = 0.f;
+            }
+    }
+    float *dst = partial + (int64_t)split * split_stride + t.out_off;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int j = t.j0 + ty * 4 + b;
+        if (j >= t.N) continue;
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = t.i0 + tx * 4 + a;
+            if (i < t.N) dst[(int64_t)j * t.N + i] = tot[b][a];
+        }
+    }
+}
+
+cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles, int ntiles,
+                            int nsplit, int32_t kper, float cell, float *partial, int64_t split_stride,
+                            cudaStream_t st) {
+    if (ntiles <= 0) return cudaSuccess;
+    dim3 grid(ntiles, nsplit);
+    k_psf_fp32<<<grid, 256, 0, st>>>(o.uv, w, ldw, o.nvis, tiles, kper, cell, partial, split_stride);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- split reduction
+// One block row per position; the partial sums of each pixel are added in float64
+// in split order (deterministic).  Partials use chunk-local packed offsets, the
+// output the caller's offsets.
+__global__ void __launch_bounds__(256) k_reduce(const float *__restrict__ partial, int nsplit,
+                                                int64_t stride, const int64_t *__restrict__ loc_offs,
+                                                const int64_t *__restrict__ out_offs,
+                                                const int32_t *__restrict__ npix, float *__restrict__ out) {
+    const int p = blockIdx.y;
+    const int64_t n2 = (int64_t)npix[p] * npix[p];
+    const float *src = partial + loc_offs[p];
+    float *dst = out + out_offs[p];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int sp = 0; sp < nsplit; ++sp) s += (double)src[(int64_t)sp * stride + q];
+        dst[q] = (float)s;
+    }
+}
+
+cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, const int64_t *loc_offs,
+                          const int64_t *out_offs, const int32_t *npix, int npos, float *out,
+                          cudaStream_t st) {
+    if (npos <= 0) return cudaSuccess;
+    dim3 grid(64, npos);
+    k_reduce<<<grid, 256, 0, st>>>(partial, nsplit, stride, loc_offs, out_offs, npix, out);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- per-visibility tables
+// uv[k] = ubar (x, y) nu_r / c in wavelengths; W[k] = tavg * favg when no weights given.
+__global__ void __launch_bounds__(256) k_fill_vis(DevObs o, float2 *__restrict__ uv, float *__restrict__ W,
+                                                  int natural) {
+    const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= o.nvis) return;
+    const int bin = k / o.nout;
+    const int r = k - bin * o.nout;
+    const float4 ub = o.bin_ubar[bin];
+    const float s = o.chan[r].x * kInvC;
+    uv[k] = make_float2(ub.x * s, ub.y * s);
+    if (natural) W[k] = (float)(o.bin_samp[bin].y * o.favg);
+}
+
+cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st) {
+    k_fill_vis<<<(o.nvis + 255) / 256, 256, 0, st>>>(o, uv, W, natural);
+    return cudaGetLastError();
+}
+
+}  // namespace psf

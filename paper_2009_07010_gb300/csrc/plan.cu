@@ -1,0 +1,584 @@
+// Host side of the C ABI: plan construction (float64 binning on the host), per-call
+// batch preparation, workspace management and dispatch to the kernels.
+//
+// Plan (Sect. 2.3, Eq. 12): every baseline's raw samples are grouped into bins of
+// tavg[b] consecutive samples (a trailing partial bin is dropped) and raw channels
+// into groups of favg.  Per bin the host forms, in float64, the mean uvw (bin
+// centre), the bin-edge delta uvw(t_e) - uvw(t_s) (Eq. 33; the edges are not
+// sampled, so (last - first) n/(n-1) for n >= 2 samples and the central
+// difference of the neighbouring samples for n = 1) and each raw sample's offset
+// from the mean.  These are rounded to float32 once and kept on the device; the
+// per-visibility tables (bin-centre uv in wavelengths, default weights) are then
+// filled by a device kernel.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <thread>
+#include <vector>
+
+#include "psf_internal.cuh"
+
+using namespace psf;
+
+namespace {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // Grow-only; contents are not preserved.
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        release();
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        bytes = n;
+        return cudaSuccess;
+    }
+};
+
+struct HostPinned {
+    void *p = nullptr;
+    size_t bytes = 0;
+    ~HostPinned() { if (p) cudaFreeHost(p); }
+    cudaError_t reserve(size_t n) {
+        if (n <= bytes) return cudaSuccess;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMallocHost(&p, n);
+        if (e != cudaSuccess) { p = nullptr; return e; }
+        bytes = n;
+        return cudaSuccess;
+    }
+};
+
+int cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return PSF_OK;
+    if (e == cudaErrorMemoryAllocation) return PSF_ENOMEM;
+    return PSF_ECUDA;
+}
+
+#define PSF_TRY(x)                         \
+    do {                                   \
+        cudaError_t e_ = (x);              \
+        if (e_ != cudaSuccess) {           \
+            cudaGetLastError();            \
+            return cuda_status(e_);        \
+        }                                  \
+    } while (0)
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+}  // namespace
+
+struct psf_plan_s {
+    psf_opts_t opts{};
+    int device = 0;
+    int nsm = 148;
+    int nbl = 0, ntime = 0, nchan = 0, favg = 1, nout = 0;
+    int64_t nbin = 0, nsamp = 0, nvis = 0;
+    DevObs d{};
+    // position-independent device arrays
+    DevBuf bin_ubar, bin_edge, bin_samp, samp, chan, rawchan, W, uv;
+    DevBuf err;          // int: device-side wait timeouts
+    // per-call workspace
+    DevBuf meta;         // positions, sizes, offsets, tiles
+    DevBuf wbuf;         // weights of a chunk of positions
+    DevBuf partial;      // split-K partial cutouts
+    HostPinned hmeta;
+    cudaEvent_t meta_done = nullptr;   // staging buffer reusable once this fires
+    // diagnostic timing (psf_profile_*)
+    bool prof = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_ev;
+    size_t prof_used = 0;
+    int64_t n_contract = 0, n_kernels = 0;
+    ~psf_plan_s() {
+        for (auto &e : prof_ev) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
+    }
+};
+
+namespace {
+
+// Host mirror of the per-call metadata layout.
+struct Meta {
+    size_t off_pos, off_npix, off_loc, off_out, off_tiles, bytes;
+};
+
+int validate_obs(const psf_obs_t *o) {
+    if (!o || o->nbl <= 0 || o->ntime <= 0 || o->nchan <= 0 || o->favg <= 0) return PSF_EINVAL;
+    if (!o->uvw_m || !o->time_s || !o->freq_hz || !o->chan_width_hz || !o->tavg) return PSF_EINVAL;
+    if (o->nchan % o->favg) return PSF_EINVAL;
+    for (int b = 0; b < o->nbl; ++b)
+        if (o->tavg[b] <= 0) return PSF_EINVAL;
+    for (int c = 0; c < o->nchan; ++c)
+        if (!(o->freq_hz[c] > 0.0) || !(o->chan_width_hz[c] > 0.0)) return PSF_EINVAL;
+    if (o->ntime >= 2) {
+        const double dt = (o->time_s[o->ntime - 1] - o->time_s[0]) / (o->ntime - 1);
+        if (!(dt > 0.0)) return PSF_EINVAL;
+        for (int t = 1; t < o->ntime; ++t)
+            if (std::fabs(o->time_s[t] - o->time_s[t - 1] - dt) > 1e-6 * dt) return PSF_EINVAL;
+    }
+    return PSF_OK;
+}
+
+int validate_opts(const psf_opts_t *op) {
+    if (!op) return PSF_OK;
+    if (op->prec != PSF_FP32 && op->prec != PSF_TC_FP16 && op->prec != PSF_TC_BF16) return PSF_EINVAL;
+    if (op->flags & ~(PSF_WTERM | PSF_IMG_LITERAL_THETA)) return PSF_EINVAL;
+    if (op->algo != PSF_ALGO_AUTO && op->algo != PSF_ALGO_CUTOUT) return PSF_EINVAL;
+    return PSF_OK;
+}
+
+template <class F>
+void parallel_for(int64_t n, F f) {
+    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+    if (n < 64 || nt == 1) {
+        for (int64_t i = 0; i < n; ++i) f(i);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t] {
+            for (int64_t i = t; i < n; i += nt) f(i);
+        });
+    for (auto &x : th) x.join();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *psf_strerror(int s) {
+    switch (s) {
+        case PSF_OK: return "ok";
+        case PSF_EINVAL: return "invalid argument";
+        case PSF_ENOMEM: return "out of memory";
+        case PSF_ECUDA: return "CUDA runtime error";
+        case PSF_EUNSUPPORTED: return "unsupported request for this path";
+        case PSF_ETIMEOUT: return "device-side wait timed out";
+        default: return "unknown status";
+    }
+}
+
+int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
+    if (!out) return PSF_EINVAL;
+    *out = nullptr;
+    int st = validate_obs(o);
+    if (st) return st;
+    if ((st = validate_opts(opts))) return st;
+
+    const int nout = o->nchan / o->favg;
+    std::vector<int64_t> bin_first(o->nbl + 1, 0), samp_first(o->nbl + 1, 0);
+    for (int b = 0; b < o->nbl; ++b) {
+        const int64_t nb = o->ntime / o->tavg[b];
+        bin_first[b + 1] = bin_first[b] + nb;
+        samp_first[b + 1] = samp_first[b] + nb * o->tavg[b];
+    }
+    const int64_t nbin = bin_first[o->nbl], nsamp = samp_first[o->nbl];
+    const int64_t nvis = nbin * nout;
+    if (nvis <= 0) return PSF_EINVAL;
+    if (nvis >= (int64_t(1) << 31)) return PSF_EUNSUPPORTED;
+
+    psf_plan_s *p = new (std::nothrow) psf_plan_s();
+    if (!p) return PSF_ENOMEM;
+    if (opts) p->opts = *opts;
+    p->nbl = o->nbl; p->ntime = o->ntime; p->nchan = o->nchan; p->favg = o->favg; p->nout = nout;
+    p->nbin = nbin; p->nsamp = nsamp; p->nvis = nvis;
+
+    auto fail = [&](int s) { delete p; return s; };
+    if (cudaGetDevice(&p->device) != cudaSuccess) { cudaGetLastError(); return fail(PSF_ECUDA); }
+    if (cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PSF_ECUDA);
+    }
+
+    // ---- float64 binning on the host, float32 records out
+    const double dt = o->ntime >= 2 ? (o->time_s[o->ntime - 1] - o->time_s[0]) / (o->ntime - 1) : 0.0;
+    std::vector<float4> h_ubar, h_edge, h_samp, h_chan, h_raw;
+    std::vector<int2> h_bs;
+    try {
+        h_ubar.resize(nbin); h_edge.resize(nbin); h_bs.resize(nbin); h_samp.resize(nsamp);
+        h_chan.resize(nout); h_raw.resize((size_t)o->nchan);
+    } catch (...) {
+        return fail(PSF_ENOMEM);
+    }
+    parallel_for(o->nbl, [&](int64_t b) {
+        const int n = o->tavg[b];
+        const double *ub = o->uvw_m + (size_t)b * o->ntime * 3;
+        const int64_t nb = bin_first[b + 1] - bin_first[b];
+        for (int64_t tau = 0; tau < nb; ++tau) {
+            const int64_t s0 = tau * n;
+            double mean[3] = {0, 0, 0}, edge[3] = {0, 0, 0};
+            for (int64_t s = s0; s < s0 + n; ++s)
+                for (int d = 0; d < 3; ++d) mean[d] += ub[s * 3 + d];
+            for (int d = 0; d < 3; ++d) mean[d] /= n;
+            if (n >= 2) {
+                for (int d = 0; d < 3; ++d)
+                    edge[d] = (ub[(s0 + n - 1) * 3 + d] - ub[s0 * 3 + d]) * (double)n / (double)(n - 1);
+            } else if (o->ntime >= 2) {
+                const int64_t sa = s0 > 0 ? s0 - 1 : s0, sb = s0 < o->ntime - 1 ? s0 + 1 : s0;
+                for (int d = 0; d < 3; ++d) edge[d] = (ub[sb * 3 + d] - ub[sa * 3 + d]) / (double)(sb - sa);
+            }
+            const int64_t bin = bin_first[b] + tau;
+            const int64_t rec = samp_first[b] + tau * n;
+            h_ubar[bin] = make_float4((float)mean[0], (float)mean[1], (float)mean[2], (float)(n * dt));
+            h_edge[bin] = make_float4((float)edge[0], (float)edge[1], (float)edge[2], 0.f);
+            h_bs[bin] = make_int2((int)rec, n);
+            for (int64_t s = 0; s < n; ++s) {
+                const double *u = ub + (s0 + s) * 3;
+                h_samp[rec + s] = make_float4((float)(u[0] - mean[0]), (float)(u[1] - mean[1]),
+                                              (float)(u[2] - mean[2]), 0.f);
+            }
+        }
+    });
+    if (nsamp >= (int64_t(1) << 31)) return fail(PSF_EUNSUPPORTED);
+    int uniform = 1;
+    for (int r = 0; r < nout; ++r) {
+        double nu = 0, dnu = 0;
+        const int c0 = r * o->favg;
+        for (int c = c0; c < c0 + o->favg; ++c) { nu += o->freq_hz[c]; dnu += o->chan_width_hz[c]; }
+        nu /= o->favg;
+        const double wd = o->chan_width_hz[c0];
+        const double sp = o->favg > 1 ? o->freq_hz[c0 + 1] - o->freq_hz[c0] : 0.0;
+        for (int c = c0; c < c0 + o->favg; ++c) {
+            if (std::fabs(o->chan_width_hz[c] - wd) > 1e-9 * wd) uniform = 0;
+            if (c > c0 && std::fabs(o->freq_hz[c] - o->freq_hz[c - 1] - sp) > 1e-9 * o->freq_hz[c]) uniform = 0;
+            h_raw[c] = make_float4((float)(o->freq_hz[c] - nu), (float)o->chan_width_hz[c],
+                                   (float)(o->chan_width_hz[c] / dnu), 0.f);
+        }
+        h_chan[r] = make_float4((float)nu, (float)dnu, (float)sp, (float)wd);
+    }
+
+    // ---- device copies
+    cudaError_t e = cudaSuccess;
+#define UP(buf, vec)                                                                               \
+    if (e == cudaSuccess) e = p->buf.reserve(std::max<size_t>(16, vec.size() * sizeof(vec[0])));   \
+    if (e == cudaSuccess && !vec.empty())                                                          \
+        e = cudaMemcpy(p->buf.p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice);
+    UP(bin_ubar, h_ubar)
+    UP(bin_edge, h_edge)
+    UP(bin_samp, h_bs)
+    UP(samp, h_samp)
+    UP(chan, h_chan)
+    UP(rawchan, h_raw)
+#undef UP
+    if (e == cudaSuccess) e = p->W.reserve(nvis * sizeof(float));
+    if (e == cudaSuccess) e = p->uv.reserve(nvis * sizeof(float2));
+    if (e == cudaSuccess) e = p->err.reserve(sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->err.p, 0, sizeof(int));
+    if (e == cudaSuccess && o->weights)
+        e = cudaMemcpy(p->W.p, o->weights, nvis * sizeof(float), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->meta_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_status(e)); }
+
+    DevObs &d = p->d;
+    d.nvis = (int32_t)nvis; d.nbin = (int32_t)nbin; d.nout = nout; d.favg = o->favg; d.uniform = uniform;
+    d.dt = (float)dt;
+    d.bin_ubar = (const float4 *)p->bin_ubar.p;
+    d.bin_edge = (const float4 *)p->bin_edge.p;
+    d.bin_samp = (const int2 *)p->bin_samp.p;
+    d.samp = (const float4 *)p->samp.p;
+    d.chan = (const float4 *)p->chan.p;
+    d.rawchan = (const float4 *)p->rawchan.p;
+    d.W = (const float *)p->W.p;
+    d.uv = (const float2 *)p->uv.p;
+    e = launch_fill_vis(d, (float2 *)p->uv.p, (float *)p->W.p, o->weights ? 0 : 1, 0);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_status(e)); }
+    *out = p;
+    return PSF_OK;
+}
+
+int psf_plan_set_opts(psf_plan_t p, const psf_opts_t *opts) {
+    if (!p || !opts) return PSF_EINVAL;
+    int st = validate_opts(opts);
+    if (st) return st;
+    p->opts = *opts;
+    return PSF_OK;
+}
+
+int64_t psf_plan_nvis(psf_plan_t p) { return p ? p->nvis : -1; }
+
+void psf_plan_destroy(psf_plan_t p) {
+    if (!p) return;
+    if (p->meta_done) {
+        cudaEventSynchronize(p->meta_done);
+        cudaEventDestroy(p->meta_done);
+    }
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+int psf_sync_status(psf_plan_t p, void *stream) {
+    if (!p) return PSF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess) { cudaGetLastError(); return PSF_ECUDA; }
+    int flag = 0;
+    if (cudaMemcpy(&flag, p->err.p, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return PSF_ECUDA;
+    }
+    if (flag) {
+        cudaMemset(p->err.p, 0, sizeof(int));
+        return PSF_ETIMEOUT;
+    }
+    return PSF_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ per-call path
+namespace {
+
+struct BatchHost {
+    int npos = 0;
+    std::vector<float4> pos;      // l0, m0, n0-1, 0
+    std::vector<int32_t> npix;
+    std::vector<int64_t> out_off;
+    double cell = 0;
+};
+
+int prepare_batch(const psf_plan_s *p, const psf_batch_t *b, BatchHost &h, int max_n) {
+    if (!b || b->npos < 0) return PSF_EINVAL;
+    h.npos = b->npos;
+    if (b->npos == 0) return PSF_OK;
+    if (!b->lm || !(b->cell_rad > 0.0)) return PSF_EINVAL;
+    if (!b->npix && b->npix0 <= 0) return PSF_EINVAL;
+    h.cell = b->cell_rad;
+    h.pos.resize(b->npos); h.npix.resize(b->npos); h.out_off.resize(b->npos);
+    int64_t run = 0;
+    for (int i = 0; i < b->npos; ++i) {
+        const int N = b->npix ? b->npix[i] : b->npix0;
+        if (N < 2 || N > 4096 || (N & 1)) return PSF_EINVAL;
+        if (N > max_n) return PSF_EUNSUPPORTED;
+        const double l0 = b->lm[2 * i], m0 = b->lm[2 * i + 1];
+        const double r2 = l0 * l0 + m0 * m0;
+        if (!(r2 < 1.0)) return PSF_EINVAL;
+        // n0 - 1 without cancellation: -(l^2+m^2) / (1 + sqrt(1 - l^2 - m^2))
+        const double n0m1 = (p->opts.flags & PSF_WTERM) ? -r2 / (1.0 + std::sqrt(1.0 - r2)) : 0.0;
+        h.pos[i] = make_float4((float)l0, (float)m0, (float)n0m1, 0.f);
+        h.npix[i] = N;
+        if (b->out_offset) {
+            if (b->out_offset[i] < 0) return PSF_EINVAL;
+            h.out_off[i] = b->out_offset[i];
+        } else {
+            h.out_off[i] = run;
+            run += (int64_t)N * N;
+        }
+    }
+    if (b->out_offset) {   // cutouts must not overlap
+        std::vector<int> idx(b->npos);
+        for (int i = 0; i < b->npos; ++i) idx[i] = i;
+        std::sort(idx.begin(), idx.end(), [&](int a, int c) { return h.out_off[a] < h.out_off[c]; });
+        for (int i = 1; i < b->npos; ++i) {
+            const int a = idx[i - 1];
+            if (h.out_off[a] + (int64_t)h.npix[a] * h.npix[a] > h.out_off[idx[i]]) return PSF_EINVAL;
+        }
+    }
+    return PSF_OK;
+}
+
+// Upload per-call metadata through a pinned staging buffer; the staging buffer is
+// reused only after the previous upload has completed.
+int upload_meta(psf_plan_s *p, const void *src, size_t bytes, cudaStream_t st) {
+    PSF_TRY(cudaEventSynchronize(p->meta_done));
+    PSF_TRY(p->hmeta.reserve(bytes));
+    PSF_TRY(p->meta.reserve(bytes));
+    std::memcpy(p->hmeta.p, src, bytes);
+    PSF_TRY(cudaMemcpyAsync(p->meta.p, p->hmeta.p, bytes, cudaMemcpyHostToDevice, st));
+    PSF_TRY(cudaEventRecord(p->meta_done, st));
+    return PSF_OK;
+}
+
+constexpr size_t kWeightBudget = size_t(4) << 30;   // weights of one position chunk (bytes)
+
+int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st) {
+    if (!p || !out) return PSF_EINVAL;
+    const bool tc = p->opts.prec != PSF_FP32;
+    BatchHost h;
+    int s = prepare_batch(p, b, h, tc ? 256 : 4096);
+    if (s || h.npos == 0) return s;
+    const int64_t K = p->nvis;
+    const int chunk = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(h.npos, 32768), kWeightBudget / (K * 8)));
+
+    for (int c0 = 0; c0 < h.npos; c0 += chunk) {
+        const int cn = std::min(chunk, h.npos - c0);
+        // chunk-local packed layout for the partial sums
+        std::vector<int64_t> loc(cn);
+        int64_t chunk_px = 0;
+        for (int i = 0; i < cn; ++i) { loc[i] = chunk_px; chunk_px += (int64_t)h.npix[c0 + i] * h.npix[c0 + i]; }
+
+        std::vector<Tile> tiles;
+        std::vector<TcItem> items;
+        int nsplit = 1, ncols_max = 16;
+        int32_t kper = (int32_t)K;
+        if (!tc) {
+            for (int i = 0; i < cn; ++i) {
+                const int N = h.npix[c0 + i];
+                for (int j0 = 0; j0 < N; j0 += 64)
+                    for (int i0 = 0; i0 < N; i0 += 64) tiles.push_back(Tile{i, N, i0, j0, loc[i]});
+            }
+            const int64_t target = 4LL * p->nsm;
+            nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((target + tiles.size() - 1) / tiles.size(),
+                                                                  (K + 4095) / 4096));
+            kper = (int32_t)(((K + nsplit - 1) / nsplit + 31) / 32 * 32);
+            nsplit = (int)((K + kper - 1) / kper);
+        } else {
+            std::vector<TcItem> base;
+            for (int i = 0; i < cn; ++i) {
+                const int N = h.npix[c0 + i];
+                for (int j0 = 0; j0 < N; j0 += 128)
+                    for (int i0 = 0; i0 < N; i0 += 256) {
+                        const int w = std::min(256, N - i0);
+                        const int nc = (w + 15) / 16 * 16;
+                        ncols_max = std::max(ncols_max, nc);
+                        base.push_back(TcItem{i, N, j0, i0, nc, 0, 0, 0, loc[i]});
+                    }
+            }
+            const int64_t target = p->nsm;
+            nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((target + base.size() - 1) / base.size(),
+                                                                  (K + 8191) / 8192));
+            kper = (int32_t)(((K + nsplit - 1) / nsplit + 31) / 32 * 32);
+            nsplit = (int)((K + kper - 1) / kper);
+            for (int sp = 0; sp < nsplit; ++sp)
+                for (auto it : base) {
+                    it.k0 = (int32_t)(sp * (int64_t)kper);
+                    it.k1 = (int32_t)std::min<int64_t>(K, (int64_t)(sp + 1) * kper);
+                    it.split = sp;
+                    items.push_back(it);
+                }
+        }
+        const bool direct = (nsplit == 1) && !tc;
+        if (direct)
+            for (auto &t : tiles) t.out_off = h.out_off[c0 + t.slot];
+
+        // metadata block: pos | npix | loc offs | out offs | tiles/items
+        Meta m;
+        m.off_pos = 0;
+        m.off_npix = align_up(m.off_pos + cn * sizeof(float4), 16);
+        m.off_loc = align_up(m.off_npix + cn * sizeof(int32_t), 16);
+        m.off_out = align_up(m.off_loc + cn * sizeof(int64_t), 16);
+        m.off_tiles = align_up(m.off_out + cn * sizeof(int64_t), 16);
+        const size_t tbytes = tc ? items.size() * sizeof(TcItem) : tiles.size() * sizeof(Tile);
+        m.bytes = align_up(m.off_tiles + tbytes, 16);
+        std::vector<char> blob(m.bytes, 0);
+        std::memcpy(blob.data() + m.off_pos, &h.pos[c0], cn * sizeof(float4));
+        std::memcpy(blob.data() + m.off_npix, &h.npix[c0], cn * sizeof(int32_t));
+        std::memcpy(blob.data() + m.off_loc, loc.data(), cn * sizeof(int64_t));
+        std::memcpy(blob.data() + m.off_out, &h.out_off[c0], cn * sizeof(int64_t));
+        if (tc) std::memcpy(blob.data() + m.off_tiles, items.data(), tbytes);
+        else std::memcpy(blob.data() + m.off_tiles, tiles.data(), tbytes);
+        if ((s = upload_meta(p, blob.data(), m.bytes, st))) return s;
+        char *dm = (char *)p->meta.p;
+        const float4 *d_pos = (const float4 *)(dm + m.off_pos);
+        const int32_t *d_npix = (const int32_t *)(dm + m.off_npix);
+        const int64_t *d_loc = (const int64_t *)(dm + m.off_loc);
+        const int64_t *d_out = (const int64_t *)(dm + m.off_out);
+
+        PSF_TRY(p->wbuf.reserve((size_t)cn * K * sizeof(float2)));
+        float2 *w = (float2 *)p->wbuf.p;
+        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, K, st));
+
+        p->n_kernels++;
+        float *part = out;
+        int64_t stride = 0;
+        if (!direct) {
+            PSF_TRY(p->partial.reserve((size_t)nsplit * chunk_px * sizeof(float)));
+            part = (float *)p->partial.p;
+            stride = chunk_px;
+        }
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        if (p->prof) {
+            if (p->prof_used == p->prof_ev.size()) {
+                cudaEvent_t a, c;
+                PSF_TRY(cudaEventCreate(&a));
+                PSF_TRY(cudaEventCreate(&c));
+                p->prof_ev.emplace_back(a, c);
+            }
+            ev1 = p->prof_ev[p->prof_used].first;
+            ev2 = p->prof_ev[p->prof_used].second;
+            p->prof_used++;
+            PSF_TRY(cudaEventRecord(ev1, st));
+        }
+        if (!tc) {
+            PSF_TRY(launch_psf_fp32(p->d, w, K, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
+                                    kper, (float)h.cell, part, stride, st));
+        } else {
+            PSF_TRY(launch_psf_tc(p->d, w, K, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
+                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, part, stride, (int *)p->err.p, st));
+        }
+        if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+        p->n_contract++;
+        p->n_kernels++;
+        if (!direct) {
+            PSF_TRY(launch_reduce(part, nsplit, stride, d_loc, d_out, d_npix, cn, out, st));
+            p->n_kernels++;
+        }
+    }
+    return PSF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int psf_exact(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
+    return run_forward(p, kExact, b, out, (cudaStream_t)stream);
+}
+int psf_approx_uv(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
+    return run_forward(p, kUV, b, out, (cudaStream_t)stream);
+}
+int psf_approx_img(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
+    return run_forward(p, kImg, b, out, (cudaStream_t)stream);
+}
+
+int psf_adjoint(psf_plan_t p, int method, const psf_batch_t *b, const float *dLdP, double *dLdlm, float *dLdW,
+                void *stream) {
+    if (!p || !dLdP || !dLdlm) return PSF_EINVAL;
+    if (method < 0 || method > 2) return PSF_EINVAL;
+    (void)b; (void)dLdW; (void)stream;
+    return PSF_EUNSUPPORTED;
+}
+
+int psf_profile_enable(psf_plan_t p, int enable) {
+    if (!p) return PSF_EINVAL;
+    p->prof = enable != 0;
+    return PSF_OK;
+}
+
+int psf_profile_read(psf_plan_t p, double *ms, int64_t *ncontract, int64_t *nkernels) {
+    if (!p) return PSF_EINVAL;
+    double tot = 0.0;
+    for (size_t i = 0; i < p->prof_used; ++i) {
+        float t = 0.f;
+        PSF_TRY(cudaEventSynchronize(p->prof_ev[i].second));
+        PSF_TRY(cudaEventElapsedTime(&t, p->prof_ev[i].first, p->prof_ev[i].second));
+        tot += t;
+    }
+    if (ms) *ms = tot;
+    if (ncontract) *ncontract = p->n_contract;
+    if (nkernels) *nkernels = p->n_kernels;
+    p->prof_used = 0;
+    p->n_contract = 0;
+    p->n_kernels = 0;
+    return PSF_OK;
+}
+
+int psf_selftest_umma(const void *a, const void *b, float *d, int n) {
+    if (!a || !b || !d || n < 16 || n > 256 || (n % 16)) return PSF_EINVAL;
+    return selftest_umma(a, b, d, n);
+}
+
+}  // extern "C"

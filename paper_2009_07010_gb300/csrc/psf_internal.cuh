@@ -1,0 +1,80 @@
+// Internal declarations shared by the library's translation units.
+// Device-resident plan arrays, per-call batch descriptors and kernel launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "psf.h"
+
+namespace psf {
+
+constexpr double kCLight = 299792458.0;   // m/s
+constexpr double kOmegaE = 7.2921150e-5;   // sidereal rate, rad/s (omega_E of Eqs. 38-41)
+
+// Position-independent arrays of a plan, float32, resident in HBM.
+// Bins are (baseline, time bin) pairs in plan order; visibility k = bin * nout + r.
+struct DevObs {
+    int32_t nvis;          // K (averaged visibilities), < 2^31
+    int32_t nbin;          // number of (baseline, time bin) pairs
+    int32_t nout;          // output channels
+    int32_t favg;          // raw channels per output channel
+    int32_t uniform;       // 1: raw channels equally spaced with equal widths in every group
+    float dt;              // raw sample spacing [s]
+    const float4 *bin_ubar;   // [nbin] bin-mean uvw [m] (x,y,z), Delta t_k [s] (w)
+    const float4 *bin_edge;   // [nbin] uvw(t_e) - uvw(t_s) [m] (Eq. 33 edges)
+    const int2 *bin_samp;     // [nbin] first raw-sample record, sample count
+    const float4 *samp;       // [nsamp] uvw_s - ubar [m] per raw sample of each bin
+    const float4 *chan;       // [nout] nu_r, Dnu_r, channel spacing, channel width
+    const float4 *rawchan;    // [nout*favg] nu_c - nu_r, dnu_c, dnu_c / Dnu_r, 0
+    const float *W;           // [nvis] visibility weights
+    const float2 *uv;         // [nvis] bin-centre (u, v) in wavelengths
+};
+
+// One cutout tile of a contraction launch.
+struct Tile {
+    int32_t slot;     // position index within the current position chunk
+    int32_t N;        // cutout size
+    int32_t i0, j0;   // first column (l offset index) / row (m offset index)
+    int64_t out_off;  // float offset of the cutout in the output
+};
+
+// Method selector (matches PSF_METHOD_*).
+enum Method { kExact = 0, kUV = 1, kImg = 2 };
+
+// ---- launchers (k_weights.cu) -------------------------------------------
+// w[s * ldw + (k - k0)] = W_k * D_k(pos[s]) for s < npos, k0 <= k < k0 + kn.
+cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos,
+                           int npos, int32_t k0, int32_t kn, float2 *w, int64_t ldw,
+                           cudaStream_t st);
+// FP32 CUDA-core contraction; partial[split * split_stride + out_off + j*N + i].
+cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles,
+                            int ntiles, int nsplit, int32_t kper, float cell, float *partial,
+                            int64_t split_stride, cudaStream_t st);
+// out[out_off_p + q] = sum_s partial[s * stride + loc_off_p + q] (float64 sum).
+cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, const int64_t *loc_offs,
+                          const int64_t *out_offs, const int32_t *npix, int npos, float *out,
+                          cudaStream_t st);
+// Plan-time per-visibility tables: uv[k] and, if natural, W[k] = tavg * favg.
+cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st);
+// Adjoint (vector-Jacobian product) in FP32, see psf_adjoint.
+cudaError_t launch_adjoint(const DevObs &o, int method, uint32_t flags, const float4 *pos,
+                           const int32_t *npix, const int64_t *offs, int npos, float cell,
+                           const float *dLdP, double *dLdlm, float *dLdW, float2 *scratch,
+                           int64_t scratch_elems, cudaStream_t st);
+
+// ---- tcgen05 contraction (k_tc.cu) ----------------------------------------
+struct TcItem {
+    int32_t slot, N;
+    int32_t j0, i0;       // first row (M) / first column (N) of the tile
+    int32_t ncols;        // tile width (multiple of 16, <= 256)
+    int32_t k0, k1;       // visibility range of this split
+    int32_t split;
+    int64_t out_off;
+};
+cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items,
+                          int nitems, int ncols_max, int bf16, float cell, float *partial,
+                          int64_t split_stride, int *err_flag, cudaStream_t st);
+int selftest_umma(const void *a, const void *b, float *d, int n);
+
+}  // namespace psf
