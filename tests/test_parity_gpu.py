@@ -4,9 +4,11 @@ Error metric: err_max = max |P - P_ref| / max |P_ref| per cutout (peak-normalise
 pointwise relative error is undefined at PSF nulls).  Tolerances:
   * configuration workloads: 1e-6 for the FP32 path, 1e-4 for the tensor-core
     path (FP16 operands);
-  * few-visibility edge cases on the tensor cores: the sum has too few terms for
-    rounding errors to average out, so the bound is a few FP16 (BF16) unit
-    roundoffs, 2^-11 (2^-8): 2e-3 (1.6e-2).
+  * few-visibility edge cases (tens of terms): the sum has too few terms for
+    rounding errors to average out, so the bound is the per-term error: a few
+    FP16 (BF16) unit roundoffs, 2^-11 (2^-8) -> 2e-3 (1.6e-2) on the tensor
+    cores; in FP32 the phase of a term is a few turns carrying ~2^-23 relative
+    error -> ~2 pi * 3 * 2^-23 ~ 2e-6, bounded at 4e-6.
 """
 import numpy as np
 import pytest
@@ -17,7 +19,7 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 TOL = {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3}
-TOL_SMALL = {"fp32": 1e-6, "tc_fp16": 2e-3, "tc_bf16": 1.6e-2}
+TOL_SMALL = {"fp32": 4e-6, "tc_fp16": 2e-3, "tc_bf16": 1.6e-2}
 METHODS = [("exact", oracle.EXACT), ("uv", oracle.UV), ("img", oracle.IMG)]
 
 
@@ -185,8 +187,6 @@ def test_config2_sampled_pixels(psf, c2, prec):
         for name, _ in METHODS:
             got = plan.forward(name, b).cpu().numpy().astype(np.float64)
             ref = refs[name]
-            peak = abs(ref[0 if sel[0] == (64 * 128 + 64) else np.argmax(np.abs(ref))])
-            peak = max(peak, np.max(np.abs(ref)))
-            e = np.max(np.abs(got[sel] - ref)) / peak
+            e = np.max(np.abs(got[sel] - ref)) / np.max(np.abs(ref))   # the centre pixel is sampled
             assert e <= TOL[prec], (name, e)
         assert plan.sync_status() == 0
