@@ -179,6 +179,9 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h"],
+                    help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
+                         "(a quarter of the visibilities, for profiler captures)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -193,7 +196,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    obs = obsgen.config2_obs()
+    obs = obsgen.config2_obs() if args.workload == "c2" else obsgen.config2_obs(hours=1.0)
     batch_g = obsgen.config2_batch()
     batch = psf.Batch.from_obsgen(batch_g)
     K = obs.nvis()
@@ -297,7 +300,7 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": {"tc_fp16": "f16", "tc_bf16": "bf16", "fp32": "f32"}[args.prec], "data": "synthetic",
-                "config": {"workload": WORKLOAD, "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
+                "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32,

@@ -161,9 +161,9 @@ def config1_batch() -> Batch:
     return Batch(np.array([[0.02, 0.02]]), np.array([64], np.int32), 2.0 * ARCSEC)
 
 
-def config2_obs() -> Observation:
+def config2_obs(hours: float = 4.0) -> Observation:
     """64-antenna array, 4 h at 1 s averaged 8:1, 16 x 0.836 MHz from 856 MHz."""
-    return _obs(meerkat_like_array(), 4 * 3600.0, 8, 856e6, 0.836e6, 16, 1)
+    return _obs(meerkat_like_array(), hours * 3600.0, 8, 856e6, 0.836e6, 16, 1)
 
 
 def config2_batch() -> Batch:

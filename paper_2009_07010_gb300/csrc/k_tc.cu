@@ -31,6 +31,7 @@ namespace psf {
 namespace {
 
 constexpr int kStages = 4;
+constexpr int kPrefetch = 6;        // stages of per-visibility inputs loaded ahead
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
 constexpr int kGenWarps = 8;
 constexpr int kDrainWarp0 = 8;
@@ -251,18 +252,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t off8[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
+        // Per-visibility inputs are prefetched kPrefetch stages ahead into a register
+        // shift queue, so global-load latency overlaps the generation of earlier stages.
+        float2 q_uv[kPrefetch], q_w[kPrefetch];
+#pragma unroll
+        for (int j = 0; j < kPrefetch; ++j) {
+            const int32_t k = it.k0 + j * kKS + lane;
+            q_uv[j] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
+            q_w[j] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
+        }
         for (int s_i = 0; s_i < nst; ++s_i) {
             const int slot = s_i % kStages;
             const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
+            const float2 uvk = q_uv[0], wk = q_w[0];
+#pragma unroll
+            for (int j = 0; j + 1 < kPrefetch; ++j) { q_uv[j] = q_uv[j + 1]; q_w[j] = q_w[j + 1]; }
+            {
+                const int32_t k = it.k0 + (s_i + kPrefetch) * kKS + lane;
+                q_uv[kPrefetch - 1] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
+                q_w[kPrefetch - 1] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
+            }
             if (s_i >= kStages) {
                 const bool ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
-            }
-            const int32_t k = it.k0 + s_i * kKS + lane;
-            float2 uvk = make_float2(0.f, 0.f), wk = make_float2(0.f, 0.f);
-            if (k < it.k1) {
-                uvk = uv[k];
-                wk = wp[k];
             }
             uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
             uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
