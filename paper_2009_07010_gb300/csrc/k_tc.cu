@@ -31,7 +31,7 @@ namespace psf {
 namespace {
 
 constexpr int kStages = 4;
-constexpr int kPrefetch = 6;        // stages of per-visibility inputs loaded ahead
+constexpr int kPrefetch = 4;        // stages of per-visibility inputs loaded ahead
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
 constexpr int kGenWarps = 8;
 constexpr int kDrainWarp0 = 8;
@@ -54,12 +54,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
                  : "memory");
 }
 
+// try_wait with a suspend-time hint: the waiting thread is parked (no issue slots)
+// until the phase completes or about kSuspendNs elapse.
+constexpr uint32_t kSuspendNs = 1000000u;
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -77,15 +81,13 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, vol
                                              int *err) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
+    for (;;) {
         if (mbar_try_wait(bar, parity)) return true;
-        if ((it & 255u) == 0) {
-            if (*abort_flag) return false;
-            if (globaltimer() - t0 > kTimeoutNs) {
-                *abort_flag = 1;
-                if (err) atomicExch(err, 1);
-                return false;
-            }
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kTimeoutNs) {
+            *abort_flag = 1;
+            if (err) atomicExch(err, 1);
+            return false;
         }
     }
 }
@@ -184,6 +186,37 @@ __device__ __forceinline__ float2 cis_turns(float x) {
     return make_float2(c, s);
 }
 
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// One 32-row twiddle chain of one visibility (this lane), rows r = 0..31 of `base`:
+// value(r) = [w] exp(2 pi i theta (n0 + r)), written as an FP16/BF16 (re, im) pair at
+// the lane's K-major swizzled slot.  The chain runs as two interleaved 16-row halves
+// (seeds at r = 0 and r = 16) so the complex recurrence uses packed FP32x2 FMAs.
+template <int BF16>
+__device__ __forceinline__ void gen_chain32(uint8_t *base, const uint32_t (&off8)[8], float theta, int n0,
+                                            float2 wk, bool weighted) {
+    float2 z0 = cis_turns(theta * (float)n0);
+    float2 z1 = cis_turns(theta * (float)(n0 + 16));
+    const float2 st = cis_turns(theta);
+    if (weighted) {
+        z0 = cmulf(z0, wk);
+        z1 = cmulf(z1, wk);
+    }
+    float2 re = make_float2(z0.x, z1.x), im = make_float2(z0.y, z1.y);
+    const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        *reinterpret_cast<uint32_t *>(base + q * 128 + off8[q & 7]) = pack2<BF16>(re.x, im.x);
+        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + off8[q & 7]) = pack2<BF16>(re.y, im.y);
+        const float2 t = __fmul2_rn(im, nsi);       // -im si
+        const float2 u = __fmul2_rn(im, sr);        //  im sr
+        im = __ffma2_rn(re, si, u);                 //  re si + im sr
+        re = __ffma2_rn(re, sr, t);                 //  re sr - im si
+    }
+}
+
 struct SmemLayout {
     uint32_t a_off, b_off, bar_off, bytes;
 };
@@ -246,14 +279,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < kGenWarps) {
         // ------------------------------------------------------------ generators
-        const int arows = 128, nA = 4, nB = (ncols + 31) / 32;
+        const int nA = 4, nB = ncols / 32;   // 32-row chains of the A (128 rows) and B tiles
         const int half = it.N / 2;
         const float2 *wp = w + (int64_t)it.slot * ldw;
         uint32_t off8[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
-        // Per-visibility inputs are prefetched kPrefetch stages ahead into a register
-        // shift queue, so global-load latency overlaps the generation of earlier stages.
+        // Per-visibility inputs are loaded kPrefetch stages ahead into registers; the
+        // stage loop is unrolled by kPrefetch so each register set is used in place.
         float2 q_uv[kPrefetch], q_w[kPrefetch];
 #pragma unroll
         for (int j = 0; j < kPrefetch; ++j) {
@@ -261,44 +294,41 @@ __global__ void __launch_bounds__(kThreads, 1)
             q_uv[j] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
             q_w[j] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
         }
-        for (int s_i = 0; s_i < nst; ++s_i) {
-            const int slot = s_i % kStages;
-            const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
-            const float2 uvk = q_uv[0], wk = q_w[0];
+        bool live = true;
+        for (int s0 = 0; s0 < nst && live; s0 += kPrefetch) {
 #pragma unroll
-            for (int j = 0; j + 1 < kPrefetch; ++j) { q_uv[j] = q_uv[j + 1]; q_w[j] = q_w[j + 1]; }
-            {
-                const int32_t k = it.k0 + (s_i + kPrefetch) * kKS + lane;
-                q_uv[kPrefetch - 1] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
-                q_w[kPrefetch - 1] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
-            }
-            if (s_i >= kStages) {
-                const bool ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
-                if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
-            }
-            uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
-            uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
-            for (int ch = warp; ch < nA + nB; ch += kGenWarps) {
-                const bool isA = ch < nA;
-                const int r0 = (isA ? ch : ch - nA) * 32;
-                const int rows = isA ? arows : ncols;
-                const float theta = (isA ? uvk.y : uvk.x) * cell;   // turns per pixel
-                const int n0 = (isA ? it.j0 : it.i0) + r0 - half;
-                float2 z = cis_turns(theta * (float)n0);
-                const float2 step = cis_turns(theta);
-                if (isA) z = make_float2(z.x * wk.x - z.y * wk.y, z.x * wk.y + z.y * wk.x);
-                const float sgn = isA ? 1.0f : -1.0f;
-                uint8_t *base = (isA ? a_tile : b_tile) + r0 * 128;
-#pragma unroll
-                for (int q = 0; q < 32; ++q) {
-                    if (r0 + q < rows)
-                        *reinterpret_cast<uint32_t *>(base + q * 128 + off8[q & 7]) = pack2<BF16>(z.x, sgn * z.y);
-                    z = make_float2(z.x * step.x - z.y * step.y, z.x * step.y + z.y * step.x);
+            for (int j = 0; j < kPrefetch; ++j) {
+                const int s_i = s0 + j;
+                if (s_i >= nst) break;
+                const float2 uvk = q_uv[j], wk = q_w[j];
+                {
+                    const int32_t k = it.k0 + (s_i + kPrefetch) * kKS + lane;
+                    q_uv[j] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
+                    q_w[j] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
                 }
+                const int slot = s_i % kStages;
+                const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
+                if (s_i >= kStages) {
+                    const bool ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
+                    if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform exit
+                        live = false;
+                        break;
+                    }
+                }
+                uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
+                uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
+                for (int ch = warp; ch < nA + nB; ch += kGenWarps) {
+                    if (ch < nA)   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
+                        gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk,
+                                          true);
+                    else           // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
+                        gen_chain32<BF16>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
+                                          it.i0 + (ch - nA) * 32 - half, wk, false);
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
             }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full[slot]);
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue

@@ -442,7 +442,7 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
                 for (int j0 = 0; j0 < N; j0 += 128)
                     for (int i0 = 0; i0 < N; i0 += 256) {
                         const int w = std::min(256, N - i0);
-                        const int nc = (w + 15) / 16 * 16;
+                        const int nc = (w + 31) / 32 * 32;   // whole 32-row twiddle chains
                         ncols_max = std::max(ncols_max, nc);
                         base.push_back(TcItem{i, N, j0, i0, nc, 0, 0, 0, loc[i]});
                     }

@@ -67,7 +67,7 @@ cudaError_t launch_adjoint(const DevObs &o, int method, uint32_t flags, const fl
 struct TcItem {
     int32_t slot, N;
     int32_t j0, i0;       // first row (M) / first column (N) of the tile
-    int32_t ncols;        // tile width (multiple of 16, <= 256)
+    int32_t ncols;        // tile width (multiple of 32, <= 256)
     int32_t k0, k1;       // visibility range of this split
     int32_t split;
     int64_t out_off;
