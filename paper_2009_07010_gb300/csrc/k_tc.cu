@@ -192,28 +192,41 @@ __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 
 // One 32-row twiddle chain of one visibility (this lane), rows r = 0..31 of `base`:
 // value(r) = [w] exp(2 pi i theta (n0 + r)), written as an FP16/BF16 (re, im) pair at
-// the lane's K-major swizzled slot.  The chain runs as two interleaved 16-row halves
-// (seeds at r = 0 and r = 16) so the complex recurrence uses packed FP32x2 FMAs.
+// the lane's K-major swizzled slot.  The chain runs as four interleaved 8-row pieces
+// (seeds at r = 0, 8, 16, 24) held in two packed FP32x2 pairs, so each step is two
+// independent packed complex multiplications.
 template <int BF16>
 __device__ __forceinline__ void gen_chain32(uint8_t *base, const uint32_t (&off8)[8], float theta, int n0,
                                             float2 wk, bool weighted) {
     float2 z0 = cis_turns(theta * (float)n0);
-    float2 z1 = cis_turns(theta * (float)(n0 + 16));
+    float2 z1 = cis_turns(theta * (float)(n0 + 8));
+    float2 z2 = cis_turns(theta * (float)(n0 + 16));
+    float2 z3 = cis_turns(theta * (float)(n0 + 24));
     const float2 st = cis_turns(theta);
     if (weighted) {
         z0 = cmulf(z0, wk);
         z1 = cmulf(z1, wk);
+        z2 = cmulf(z2, wk);
+        z3 = cmulf(z3, wk);
     }
-    float2 re = make_float2(z0.x, z1.x), im = make_float2(z0.y, z1.y);
+    float2 reA = make_float2(z0.x, z2.x), imA = make_float2(z0.y, z2.y);   // rows q, q + 16
+    float2 reB = make_float2(z1.x, z3.x), imB = make_float2(z1.y, z3.y);   // rows q + 8, q + 24
     const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
 #pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        *reinterpret_cast<uint32_t *>(base + q * 128 + off8[q & 7]) = pack2<BF16>(re.x, im.x);
-        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + off8[q & 7]) = pack2<BF16>(re.y, im.y);
-        const float2 t = __fmul2_rn(im, nsi);       // -im si
-        const float2 u = __fmul2_rn(im, sr);        //  im sr
-        im = __ffma2_rn(re, si, u);                 //  re si + im sr
-        re = __ffma2_rn(re, sr, t);                 //  re sr - im si
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t o = off8[q];
+        *reinterpret_cast<uint32_t *>(base + q * 128 + o) = pack2<BF16>(reA.x, imA.x);
+        *reinterpret_cast<uint32_t *>(base + (q + 8) * 128 + o) = pack2<BF16>(reB.x, imB.x);
+        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + o) = pack2<BF16>(reA.y, imA.y);
+        *reinterpret_cast<uint32_t *>(base + (q + 24) * 128 + o) = pack2<BF16>(reB.y, imB.y);
+        if (q < 7) {
+            const float2 tA = __fmul2_rn(imA, nsi), uA = __fmul2_rn(imA, sr);
+            const float2 tB = __fmul2_rn(imB, nsi), uB = __fmul2_rn(imB, sr);
+            imA = __ffma2_rn(reA, si, uA);
+            reA = __ffma2_rn(reA, sr, tA);
+            imB = __ffma2_rn(reB, si, uB);
+            reB = __ffma2_rn(reB, sr, tB);
+        }
     }
 }
 
@@ -287,12 +300,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
         // Per-visibility inputs are loaded kPrefetch stages ahead into registers; the
         // stage loop is unrolled by kPrefetch so each register set is used in place.
+        // Loads use a clamped index and are never predicated, so no instruction needs
+        // the loaded value before it is consumed; out-of-range lanes get w = 0 at use.
         float2 q_uv[kPrefetch], q_w[kPrefetch];
+        const int32_t klast = max(it.k1 - 1, it.k0);
 #pragma unroll
         for (int j = 0; j < kPrefetch; ++j) {
-            const int32_t k = it.k0 + j * kKS + lane;
-            q_uv[j] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
-            q_w[j] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
+            const int32_t k = min(it.k0 + j * kKS + lane, klast);
+            if (nst > 0) {
+                q_uv[j] = __ldg(&uv[k]);
+                q_w[j] = __ldg(&wp[k]);
+            }
         }
         bool live = true;
         for (int s0 = 0; s0 < nst && live; s0 += kPrefetch) {
@@ -300,11 +318,12 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int j = 0; j < kPrefetch; ++j) {
                 const int s_i = s0 + j;
                 if (s_i >= nst) break;
-                const float2 uvk = q_uv[j], wk = q_w[j];
+                const float2 uvk = q_uv[j];
+                const float2 wk = (it.k0 + s_i * kKS + lane < it.k1) ? q_w[j] : make_float2(0.f, 0.f);
                 {
-                    const int32_t k = it.k0 + (s_i + kPrefetch) * kKS + lane;
-                    q_uv[j] = k < it.k1 ? __ldg(&uv[k]) : make_float2(0.f, 0.f);
-                    q_w[j] = k < it.k1 ? __ldg(&wp[k]) : make_float2(0.f, 0.f);
+                    const int32_t k = min(it.k0 + (s_i + kPrefetch) * kKS + lane, klast);
+                    q_uv[j] = __ldg(&uv[k]);
+                    q_w[j] = __ldg(&wp[k]);
                 }
                 const int slot = s_i % kStages;
                 const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
