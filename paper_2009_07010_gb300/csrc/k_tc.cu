@@ -30,13 +30,14 @@
 namespace psf {
 namespace {
 
-constexpr int kStages = 4;
-constexpr int kPrefetch = 4;        // stages of per-visibility inputs loaded ahead
+constexpr int kStages = 4;         // operand (A/B tile) pipeline depth
+constexpr int kInStages = 8;       // per-visibility input (uv, w) ring depth
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
-constexpr int kGenWarps = 8;
-constexpr int kDrainWarp0 = 8;
-constexpr int kMmaWarp = 12;
-constexpr int kThreads = 13 * 32;
+constexpr int kGenWarps = 16;      // two groups of 8, taking alternate stages
+constexpr int kGroupWarps = 8;
+constexpr int kDrainWarp0 = 16;
+constexpr int kMmaWarp = 20;
+constexpr int kThreads = 21 * 32;
 constexpr int kDrainStages = 64;   // stages accumulated in TMEM between drains
 constexpr int kATileBytes = 128 * 128;
 constexpr unsigned long long kTimeoutNs = 2000000000ull;
@@ -90,6 +91,23 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, vol
             return false;
         }
     }
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(
+                     smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// Bulk (non-tensor) async copy global -> shared, completing `bytes` on `bar`.
+// Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async_smem() {
@@ -231,15 +249,18 @@ __device__ __forceinline__ void gen_chain32(uint8_t *base, const uint32_t (&off8
 }
 
 struct SmemLayout {
-    uint32_t a_off, b_off, bar_off, bytes;
+    uint32_t a_off, b_off, in_off, bar_off, bytes;
 };
+
+constexpr uint32_t kInSlotBytes = kKS * 16;   // uv (8 B) + w (8 B) per visibility
 
 __host__ __device__ inline SmemLayout smem_layout(int ncols_max) {
     SmemLayout L;
     const uint32_t bt = (uint32_t)ncols_max * 128u;
     L.a_off = 0;
     L.b_off = kStages * kATileBytes;
-    L.bar_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
+    L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
+    L.bar_off = L.in_off + kInStages * kInSlotBytes;
     L.bytes = L.bar_off + 256;
     return L;
 }
@@ -255,7 +276,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const SmemLayout L = smem_layout(ncols_max);
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
     uint64_t *empty = full + kStages;
-    uint64_t *acc_full = empty + kStages;
+    uint64_t *in_full = empty + kStages;
+    uint64_t *acc_full = in_full + kInStages;
     uint64_t *acc_empty = acc_full + 2;
     uint64_t *done_bar = acc_empty + 2;
     uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
@@ -270,9 +292,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], kGenWarps);
+            mbar_init(&full[s], kGroupWarps);
             mbar_init(&empty[s], 1);
         }
+        for (int s = 0; s < kInStages; ++s) mbar_init(&in_full[s], 1);
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
             mbar_init(&acc_empty[a], 4);
@@ -292,62 +315,37 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp < kGenWarps) {
         // ------------------------------------------------------------ generators
+        const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
         const int nA = 4, nB = ncols / 32;   // 32-row chains of the A (128 rows) and B tiles
         const int half = it.N / 2;
-        const float2 *wp = w + (int64_t)it.slot * ldw;
         uint32_t off8[8];
 #pragma unroll
         for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
-        // Per-visibility inputs are loaded kPrefetch stages ahead into registers; the
-        // stage loop is unrolled by kPrefetch so each register set is used in place.
-        // Loads use a clamped index and are never predicated, so no instruction needs
-        // the loaded value before it is consumed; out-of-range lanes get w = 0 at use.
-        float2 q_uv[kPrefetch], q_w[kPrefetch];
-        const int32_t klast = max(it.k1 - 1, it.k0);
-#pragma unroll
-        for (int j = 0; j < kPrefetch; ++j) {
-            const int32_t k = min(it.k0 + j * kKS + lane, klast);
-            if (nst > 0) {
-                q_uv[j] = __ldg(&uv[k]);
-                q_w[j] = __ldg(&wp[k]);
+        for (int s_i = grp; s_i < nst; s_i += 2) {
+            const int slot = s_i % kStages;
+            const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
+            const int islot = s_i % kInStages;
+            bool ok = wait_bounded(&in_full[islot], (uint32_t)(s_i / kInStages) & 1u, s_abort, err);
+            if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
+            const float2 *in_uv = (const float2 *)(smem + L.in_off + islot * kInSlotBytes);
+            const float2 uvk = in_uv[lane];
+            const float2 wk = (it.k0 + s_i * kKS + lane < it.k1) ? in_uv[kKS + lane] : make_float2(0.f, 0.f);
+            if (s_i >= kStages) {
+                ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
+                if (!__all_sync(0xffffffffu, ok)) break;
             }
-        }
-        bool live = true;
-        for (int s0 = 0; s0 < nst && live; s0 += kPrefetch) {
-#pragma unroll
-            for (int j = 0; j < kPrefetch; ++j) {
-                const int s_i = s0 + j;
-                if (s_i >= nst) break;
-                const float2 uvk = q_uv[j];
-                const float2 wk = (it.k0 + s_i * kKS + lane < it.k1) ? q_w[j] : make_float2(0.f, 0.f);
-                {
-                    const int32_t k = min(it.k0 + (s_i + kPrefetch) * kKS + lane, klast);
-                    q_uv[j] = __ldg(&uv[k]);
-                    q_w[j] = __ldg(&wp[k]);
-                }
-                const int slot = s_i % kStages;
-                const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
-                if (s_i >= kStages) {
-                    const bool ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
-                    if (!__all_sync(0xffffffffu, ok)) {   // warp-uniform exit
-                        live = false;
-                        break;
-                    }
-                }
-                uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
-                uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
-                for (int ch = warp; ch < nA + nB; ch += kGenWarps) {
-                    if (ch < nA)   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
-                        gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk,
-                                          true);
-                    else           // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
-                        gen_chain32<BF16>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
-                                          it.i0 + (ch - nA) * 32 - half, wk, false);
-                }
-                fence_proxy_async_smem();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(&full[slot]);
+            uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
+            uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
+            for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
+                if (ch < nA)   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
+                    gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk, true);
+                else           // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
+                    gen_chain32<BF16>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
+                                      it.i0 + (ch - nA) * 32 - half, wk, false);
             }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[slot]);
         }
     } else if (warp == kMmaWarp) {
         // ------------------------------------------------------------ MMA issue
@@ -356,10 +354,23 @@ __global__ void __launch_bounds__(kThreads, 1)
             int acc = 0, in_acc = 0;
             int uses[2] = {0, 0};
             const uint32_t a0 = smem_u32(smem + L.a_off), b0 = smem_u32(smem + L.b_off);
+            // input ring: stage s's uv and w (256 B each) into slot s % kInStages
+            const float2 *wp = w + (int64_t)it.slot * ldw;
+            auto load_inputs = [&](int s) {
+                const int islot = s % kInStages;
+                uint8_t *dst = smem + L.in_off + islot * kInSlotBytes;
+                const int32_t kb = it.k0 + s * kKS;
+                mbar_arrive_expect_tx(&in_full[islot], kInSlotBytes);
+                bulk_g2s(dst, uv + kb, kKS * 8, &in_full[islot]);
+                bulk_g2s(dst + kKS * 8, wp + kb, kKS * 8, &in_full[islot]);
+            };
+            for (int s = 0; s < kInStages && s < nst; ++s) load_inputs(s);
             for (int s_i = 0; s_i < nst; ++s_i) {
                 const int slot = s_i % kStages;
                 const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
                 if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
+                // the generators of stage s_i have read its inputs: refill the slot
+                if (s_i + kInStages < nst) load_inputs(s_i + kInStages);
                 if (in_acc == 0 && uses[acc] > 0 &&
                     !wait_bounded(&acc_empty[acc], (uint32_t)(uses[acc] - 1) & 1u, s_abort, err))
                     break;

@@ -274,7 +274,10 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     UP(rawchan, h_raw)
 #undef UP
     if (e == cudaSuccess) e = p->W.reserve(nvis * sizeof(float));
-    if (e == cudaSuccess) e = p->uv.reserve(nvis * sizeof(float2));
+    // uv is padded with zeros to a whole number of 32-visibility stages plus one
+    // stage, so bulk copies of full stages never leave the buffer
+    if (e == cudaSuccess) e = p->uv.reserve((size_t)(nvis + 64) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(p->uv.p, 0, (size_t)(nvis + 64) * sizeof(float2));
     if (e == cudaSuccess) e = p->err.reserve(sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->err.p, 0, sizeof(int));
     if (e == cudaSuccess && o->weights)
@@ -487,9 +490,12 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
         const int64_t *d_loc = (const int64_t *)(dm + m.off_loc);
         const int64_t *d_out = (const int64_t *)(dm + m.off_out);
 
-        PSF_TRY(p->wbuf.reserve((size_t)cn * K * sizeof(float2)));
+        // weight rows padded to 32 visibilities (16-byte aligned stage copies), plus
+        // one stage of slack after the last row
+        const int64_t ldw = (K + 31) / 32 * 32;
+        PSF_TRY(p->wbuf.reserve((size_t)(cn * ldw + 64) * sizeof(float2)));
         float2 *w = (float2 *)p->wbuf.p;
-        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, K, st));
+        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, st));
 
         p->n_kernels++;
         float *part = out;
@@ -513,10 +519,10 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
             PSF_TRY(cudaEventRecord(ev1, st));
         }
         if (!tc) {
-            PSF_TRY(launch_psf_fp32(p->d, w, K, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
+            PSF_TRY(launch_psf_fp32(p->d, w, ldw, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
                                     kper, (float)h.cell, part, stride, st));
         } else {
-            PSF_TRY(launch_psf_tc(p->d, w, K, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
+            PSF_TRY(launch_psf_tc(p->d, w, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
                                   p->opts.prec == PSF_TC_BF16, (float)h.cell, part, stride, (int *)p->err.p, st));
         }
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
