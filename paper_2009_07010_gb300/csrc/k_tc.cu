@@ -30,8 +30,7 @@
 namespace psf {
 namespace {
 
-constexpr int kStages = 4;         // operand (A/B tile) pipeline depth
-constexpr int kInStages = 8;       // per-visibility input (uv, w) ring depth
+constexpr int kInStages = 16;      // per-visibility input (uv, w) ring depth
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
 constexpr int kGenWarps = 16;      // two groups of 8, taking alternate stages
 constexpr int kGroupWarps = 8;
@@ -55,19 +54,29 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
                  : "memory");
 }
 
-// try_wait with a suspend-time hint: the waiting thread is parked (no issue slots)
-// until the phase completes or about kSuspendNs elapse.
-constexpr uint32_t kSuspendNs = 1000000u;
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+// try_wait; with a nonzero suspend-time hint the waiting thread is parked (no issue
+// slots) until the phase completes or about `hint_ns` elapse.  Latency-critical
+// pipeline waits use no hint; the long drain waits sleep.
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
-        : "memory");
+    if (hint_ns) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+    }
     return ok != 0;
 }
+constexpr uint32_t kSpin = 0u, kSleepNs = 1000000u;
 
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
@@ -79,11 +88,12 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // aborting or the wall-clock limit expired (then the abort flag and the global
 // error flag are raised).
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                             int *err) {
-    if (mbar_try_wait(bar, parity)) return true;
+                                             int *err, uint32_t hint_ns = kSpin) {
+    if (mbar_try_wait(bar, parity, hint_ns)) return true;
     const unsigned long long t0 = globaltimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
+    for (uint32_t it = 1;; ++it) {
+        if (mbar_try_wait(bar, parity, hint_ns)) return true;
+        if (!hint_ns && (it & 63u)) continue;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kTimeoutNs) {
             *abort_flag = 1;
@@ -254,18 +264,24 @@ struct SmemLayout {
 
 constexpr uint32_t kInSlotBytes = kKS * 16;   // uv (8 B) + w (8 B) per visibility
 
-__host__ __device__ inline SmemLayout smem_layout(int ncols_max) {
+// Operand ring depth for a tile width: as many 128-row A + ncols-row B stages as fit
+// in ~192 KB (4 at 256 columns, 6 at 128, 8 at <= 64).
+__host__ __device__ constexpr int stages_for(int ncols_max) {
+    return ncols_max > 128 ? 4 : (ncols_max > 64 ? 6 : 8);
+}
+
+__host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
     SmemLayout L;
     const uint32_t bt = (uint32_t)ncols_max * 128u;
     L.a_off = 0;
     L.b_off = kStages * kATileBytes;
     L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
     L.bar_off = L.in_off + kInStages * kInSlotBytes;
-    L.bytes = L.bar_off + 256;
+    L.bytes = L.bar_off + 512;   // 2 S + kInStages + 5 barriers (<= 37 x 8 B), TMEM address, abort flag
     return L;
 }
 
-template <int BF16>
+template <int BF16, int kStages>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
              const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
@@ -273,7 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the operand tiles (swizzle atoms)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const SmemLayout L = smem_layout(ncols_max);
+    const SmemLayout L = smem_layout(ncols_max, kStages);
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
     uint64_t *empty = full + kStages;
     uint64_t *in_full = empty + kStages;
@@ -392,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // all issued MMAs complete before TMEM is released
             umma_commit(done_bar);
-            wait_bounded(done_bar, 0, s_abort, nullptr);
+            wait_bounded(done_bar, 0, s_abort, nullptr, kSleepNs);
         }
         __syncwarp();
     } else {
@@ -409,7 +425,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
         for (int d = 0; d < ndrain; ++d) {
             const int acc = d & 1;
-            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err);
+            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err, kSleepNs);
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
@@ -499,25 +515,29 @@ __global__ void __launch_bounds__(128, 1)
 
 }  // namespace
 
+template <int BF16, int S>
+static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
+                               int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
+                               cudaStream_t st) {
+    const SmemLayout L = smem_layout(ncols_max, S);
+    const size_t bytes = L.bytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e != cudaSuccess) return e;
+    k_psf_tc<BF16, S><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
+                                                        err);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                           int ncols_max, int bf16, float cell, float *partial, int64_t split_stride, int *err,
                           cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
-    const SmemLayout L = smem_layout(ncols_max);
-    const size_t bytes = L.bytes + 1024;
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(k_psf_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        k_psf_tc<1><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
-                                                     err);
-    } else {
-        e = cudaFuncSetAttribute(k_psf_tc<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-        if (e != cudaSuccess) return e;
-        k_psf_tc<0><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
-                                                     err);
-    }
-    return cudaGetLastError();
+    const int S = stages_for(ncols_max);
+#define PSF_TC_CASE(B, SS) \
+    if (bf16 == B && S == SS) return launch_tc_t<B, SS>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err, st);
+    PSF_TC_CASE(0, 4) PSF_TC_CASE(0, 6) PSF_TC_CASE(0, 8) PSF_TC_CASE(1, 4) PSF_TC_CASE(1, 6) PSF_TC_CASE(1, 8)
+#undef PSF_TC_CASE
+    return cudaErrorInvalidValue;
 }
 
 int selftest_umma(const void *a, const void *b, float *d, int n) {
