@@ -78,6 +78,18 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, ui
 }
 constexpr uint32_t kSpin = 0u, kSleepNs = 1000000u;
 
+// Non-blocking probe of a phase (never suspends the thread).
+__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
 __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -89,6 +101,10 @@ __device__ __forceinline__ unsigned long long globaltimer() {
 // error flag are raised).
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
                                              int *err, uint32_t hint_ns = kSpin) {
+    if (!hint_ns) {   // latency-critical: poll without suspending first
+        for (int i = 0; i < 4096; ++i)
+            if (mbar_test_wait(bar, parity)) return true;
+    }
     if (mbar_try_wait(bar, parity, hint_ns)) return true;
     const unsigned long long t0 = globaltimer();
     for (uint32_t it = 1;; ++it) {
