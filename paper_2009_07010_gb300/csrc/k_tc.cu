@@ -55,8 +55,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
 }
 
 // try_wait; with a nonzero suspend-time hint the waiting thread is parked (no issue
-// slots) until the phase completes or about `hint_ns` elapse.  Latency-critical
-// pipeline waits use no hint; the long drain waits sleep.
+// slots) until the phase completes or about `hint_ns` elapse.  Measured on GB300,
+// parked waits beat polling for every role of this kernel (polling warps take
+// issue slots from the generators).
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, uint32_t hint_ns) {
     uint32_t ok;
     if (hint_ns) {
@@ -76,40 +77,17 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, ui
     }
     return ok != 0;
 }
-constexpr uint32_t kSpin = 0u, kSleepNs = 1000000u;
-
-// Non-blocking probe of a phase (never suspends the thread).
-__device__ __forceinline__ bool mbar_test_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long globaltimer() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
+constexpr uint32_t kSleepNs = 1000000u;
 
 // Wait for the phase of `bar` with the given parity.  Returns false if the CTA is
 // aborting or the wall-clock limit expired (then the abort flag and the global
 // error flag are raised).
 __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, volatile int *abort_flag,
-                                             int *err, uint32_t hint_ns = kSpin) {
-    if (!hint_ns) {   // latency-critical: poll without suspending first
-        for (int i = 0; i < 4096; ++i)
-            if (mbar_test_wait(bar, parity)) return true;
-    }
+                                             int *err, uint32_t hint_ns = kSleepNs) {
     if (mbar_try_wait(bar, parity, hint_ns)) return true;
     const unsigned long long t0 = globaltimer();
-    for (uint32_t it = 1;; ++it) {
+    for (;;) {
         if (mbar_try_wait(bar, parity, hint_ns)) return true;
-        if (!hint_ns && (it & 63u)) continue;
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kTimeoutNs) {
             *abort_flag = 1;
@@ -424,7 +402,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             // all issued MMAs complete before TMEM is released
             umma_commit(done_bar);
-            wait_bounded(done_bar, 0, s_abort, nullptr, kSleepNs);
+            wait_bounded(done_bar, 0, s_abort, nullptr);
         }
         __syncwarp();
     } else {
@@ -441,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
         for (int d = 0; d < ndrain; ++d) {
             const int acc = d & 1;
-            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err, kSleepNs);
+            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err);
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
