@@ -79,6 +79,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity, ui
 }
 constexpr uint32_t kSleepNs = 1000000u;
 
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Wait for the phase of `bar` with the given parity.  Returns false if the CTA is
 // aborting or the wall-clock limit expired (then the abort flag and the global
 // error flag are raised).
