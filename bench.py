@@ -35,6 +35,20 @@ sys.path.insert(0, ROOT)
 import obsgen  # noqa: E402
 
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
+# DRAM bytes (read + write) per contraction launch from the ncu capture summarised in
+# profiles/k_psf_tc_meerkat64_1h_128px.md, per visibility (traffic is proportional to
+# K), valid only for the kernel source it was taken on.
+PROFILED_TRAFFIC = {"kernel_sha256_prefix": "f1506bd5cb681118", "bytes_per_vis": (232.446464e6 + 3.767552e6) / 14515200,
+                    "profile": "profiles/k_psf_tc_meerkat64_1h_128px.md"}
+
+
+def profiled_traffic(nvis):
+    import hashlib
+    src = os.path.join(ROOT, "paper_2009_07010_gb300", "csrc", "k_tc.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != PROFILED_TRAFFIC["kernel_sha256_prefix"]:
+        return None
+    return PROFILED_TRAFFIC["bytes_per_vis"] * nvis
 WORKLOAD = "meerkat64_4h_16ch_128px_single_cutout"
 
 
@@ -291,8 +305,10 @@ def main():
         avg_ms = kms / launches
         flops_launch = 4.0 * K * batch.total()
         achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+        traffic = profiled_traffic(K)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": src,
+                "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
+                "traffic_source": PROFILED_TRAFFIC["profile"] if traffic else None, "peak_source": src,
                 "kernel": "k_psf_tc (tcgen05 contraction)", "avg_launch_ms": avg_ms,
                 "algorithmic_flops_per_launch": flops_launch}
         cpu = None if args.no_cpu_baseline else cpu_baseline_sample(obs, batch_g)
