@@ -20,7 +20,7 @@ EXACT, UV, IMG = 0, 1, 2
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
            "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
-           "psf_strerror", "psf_selftest_umma"]
+           "psf_strerror", "psf_selftest_umma", "psf_exact_noalloc"]
 
 
 class PsfError(RuntimeError):

@@ -582,6 +582,16 @@ int psf_profile_read(psf_plan_t p, double *ms, int64_t *ncontract, int64_t *nker
     return PSF_OK;
 }
 
+}  // extern "C"
+
+// Read-only views of a plan for other translation units of the library.
+namespace psf {
+const DevObs *plan_devobs(psf_plan_t p) { return p ? &p->d : nullptr; }
+uint32_t plan_flags(psf_plan_t p) { return p ? p->opts.flags : 0u; }
+}  // namespace psf
+
+extern "C" {
+
 int psf_selftest_umma(const void *a, const void *b, float *d, int n) {
     if (!a || !b || !d || n < 16 || n > 256 || (n % 16)) return PSF_EINVAL;
     return selftest_umma(a, b, d, n);

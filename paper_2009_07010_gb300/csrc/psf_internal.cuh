@@ -77,4 +77,8 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
                           int64_t split_stride, int *err_flag, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
 
+// Read-only views of a plan (plan.cu).
+const DevObs *plan_devobs(psf_plan_t p);
+uint32_t plan_flags(psf_plan_t p);
+
 }  // namespace psf
