@@ -5,5 +5,5 @@ include/psf.h.
 """
 from ._lib import (EXACT, IMG, PSF_ALGO_AUTO, PSF_ALGO_CUTOUT, PSF_IMG_LITERAL_THETA, PSF_WTERM, UV,  # noqa: F401
                    PsfError, lib)
-from .api import Batch, Plan, selftest_umma  # noqa: F401
+from .api import Batch, Plan, SmearedPSF, selftest_umma, smeared_psf  # noqa: F401
 from .build import build as build_library  # noqa: F401

@@ -163,3 +163,31 @@ def selftest_umma(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     check(_lib.lib().psf_selftest_umma(ctypes.c_void_p(a.data_ptr()), ctypes.c_void_p(b.data_ptr()),
                                        ctypes.c_void_p(d.data_ptr()), b.shape[0]), "psf_selftest_umma")
     return d
+
+
+class SmearedPSF(torch.autograd.Function):
+    """Cutouts as a differentiable function of the positions (l0, m0).
+
+    forward(lm) evaluates `method` on the plan's observation; backward runs the
+    library's adjoint (psf_adjoint) on the incoming gradient.  lm is a float64 host
+    tensor [npos, 2] (positions are host inputs of the C ABI); the returned gradient
+    lives on the same device as lm.
+    """
+
+    @staticmethod
+    def forward(ctx, lm, plan, method, npix, cell):
+        batch = Batch(lm.detach().cpu().numpy(), npix, cell)
+        out = plan.forward(method, batch)[:batch.total()]
+        ctx.plan, ctx.method, ctx.batch, ctx.lm_device = plan, method, batch, lm.device
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g = grad_out.detach().to(torch.float32).contiguous()
+        g_lm, _ = ctx.plan.adjoint(ctx.method, ctx.batch, g, want_dW=False)
+        return g_lm.to(ctx.lm_device), None, None, None, None
+
+
+def smeared_psf(plan: Plan, method: str, lm: torch.Tensor, npix, cell: float) -> torch.Tensor:
+    """Differentiable cutouts of `method` at positions lm (see SmearedPSF)."""
+    return SmearedPSF.apply(lm, plan, method, npix, cell)

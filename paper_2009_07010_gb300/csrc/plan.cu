@@ -554,8 +554,52 @@ int psf_adjoint(psf_plan_t p, int method, const psf_batch_t *b, const float *dLd
                 void *stream) {
     if (!p || !dLdP || !dLdlm) return PSF_EINVAL;
     if (method < 0 || method > 2) return PSF_EINVAL;
-    (void)b; (void)dLdW; (void)stream;
-    return PSF_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    BatchHost h;
+    int s = prepare_batch(p, b, h, adjoint_max_n());
+    if (s) return s;
+    if (h.npos == 0) {
+        if (dLdW) PSF_TRY(cudaMemsetAsync(dLdW, 0, p->nvis * sizeof(float), st));
+        return PSF_OK;
+    }
+    const int64_t ncta = adjoint_ctas(p->nvis);
+    const int64_t budget = int64_t(512) << 20;
+    const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(h.npos, budget / (ncta * 16)));
+    struct AdjPosHost { float4 L, dLl, dLm; };
+    for (int c0 = 0; c0 < h.npos; c0 += chunk) {
+        const int cn = std::min(chunk, h.npos - c0);
+        int nmax = 2;
+        std::vector<AdjPosHost> ap(cn);
+        for (int i = 0; i < cn; ++i) {
+            const double l0 = b->lm[2 * (c0 + i)], m0 = b->lm[2 * (c0 + i) + 1];
+            float dzl = 0.f, dzm = 0.f;
+            if (p->opts.flags & PSF_WTERM) {   // d(n0 - 1)/dl0 = -l0 / n0
+                const double n0 = std::sqrt(1.0 - l0 * l0 - m0 * m0);
+                dzl = (float)(-l0 / n0);
+                dzm = (float)(-m0 / n0);
+            }
+            ap[i].L = h.pos[c0 + i];
+            ap[i].dLl = make_float4(1.f, 0.f, dzl, 0.f);
+            ap[i].dLm = make_float4(0.f, 1.f, dzm, 0.f);
+            nmax = std::max(nmax, (int)h.npix[c0 + i]);
+        }
+        const size_t off_pos = 0;
+        const size_t off_npix = align_up(off_pos + cn * sizeof(AdjPosHost), 16);
+        const size_t off_offs = align_up(off_npix + cn * sizeof(int32_t), 16);
+        const size_t bytes = align_up(off_offs + cn * sizeof(int64_t), 16);
+        std::vector<char> blob(bytes, 0);
+        std::memcpy(blob.data() + off_pos, ap.data(), cn * sizeof(AdjPosHost));
+        std::memcpy(blob.data() + off_npix, &h.npix[c0], cn * sizeof(int32_t));
+        std::memcpy(blob.data() + off_offs, &h.out_off[c0], cn * sizeof(int64_t));
+        if ((s = upload_meta(p, blob.data(), bytes, st))) return s;
+        char *dm = (char *)p->meta.p;
+        PSF_TRY(p->partial.reserve((size_t)ncta * cn * 2 * sizeof(double)));
+        PSF_TRY(launch_adjoint_chunk(p->d, method, p->opts.flags, dm + off_pos, (const int32_t *)(dm + off_npix),
+                                     (const int64_t *)(dm + off_offs), cn, nmax, (float)h.cell, dLdP, dLdW,
+                                     c0 > 0, (double *)p->partial.p, dLdlm + 2 * c0, st));
+        p->n_kernels += 2;
+    }
+    return PSF_OK;
 }
 
 int psf_profile_enable(psf_plan_t p, int enable) {

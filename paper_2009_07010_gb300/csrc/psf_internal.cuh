@@ -57,11 +57,13 @@ cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, cons
                           cudaStream_t st);
 // Plan-time per-visibility tables: uv[k] and, if natural, W[k] = tavg * favg.
 cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st);
-// Adjoint (vector-Jacobian product) in FP32, see psf_adjoint.
-cudaError_t launch_adjoint(const DevObs &o, int method, uint32_t flags, const float4 *pos,
-                           const int32_t *npix, const int64_t *offs, int npos, float cell,
-                           const float *dLdP, double *dLdlm, float *dLdW, float2 *scratch,
-                           int64_t scratch_elems, cudaStream_t st);
+// Adjoint (vector-Jacobian product) in FP32, see psf_adjoint (k_adjoint.cu).
+// pos: [npos] {L, dL/dl0, dL/dm0} float4 triples; partial: [ctas][npos][2] doubles.
+int adjoint_max_n();
+int64_t adjoint_ctas(int64_t nvis);
+cudaError_t launch_adjoint_chunk(const DevObs &o, int method, uint32_t flags, const void *pos, const int32_t *npix,
+                                 const int64_t *offs, int npos, int nmax, float cell, const float *R, float *gW,
+                                 int accumulate_gW, double *partial, double *g_lm, cudaStream_t st);
 
 // ---- tcgen05 contraction (k_tc.cu) ----------------------------------------
 struct TcItem {
