@@ -1,0 +1,290 @@
+// Batched (Khatri-Rao) tcgen05 contraction: many positions with the same cutout size.
+//
+//   X[p][q] = sum_k Re( w_{p,k} KR_k[q] ),   KR_k[q] = exp(2 pi i (u_k dl_i + v_k dm_j)),
+//   pixel q = j N + i,  w_{p,k} = W_k D_k(l0_p)                         (Eqs. 21-22)
+//
+// As a real GEMM with K' = 2K: A'[p][2k] = Re w, A'[p][2k+1] = -Im w (the weights,
+// precomputed per position chunk into an FP16/BF16 buffer and loaded by 2-D TMA with
+// 128-byte swizzle), B'[q][2k] = Re KR, B'[q][2k+1] = Im KR (generated on chip).
+// One CTA computes a 128-position x 256-pixel tile over a range of visibilities:
+//   warps 0-7    generate the 256 pixel twiddles of each 32-visibility stage: each
+//                lane owns one visibility and walks a 32-pixel run of one cutout row
+//                (phasor recurrence along l, seeded from the MUFU sine/cosine of the
+//                reduced phase u dl + v dm), FP16/BF16 pairs into the swizzled layout;
+//   warp 12      TMA producer of the weight tile of each stage;
+//   warp 13      TMEM allocation, the uv input ring (bulk copies) and the single-thread
+//                tcgen05.mma issue (M = 128, N = 256, K = 16);
+//   warps 8-11   every kFoldStages stages add the active TMEM accumulator into a
+//                running-sum region of TMEM (short FP32 accumulation runs); at the
+//                end they add sum + active into the output with global atomics (the
+//                output is zeroed first; several visibility ranges of a tile add up).
+// Every barrier wait is bounded (2 s); on expiry the CTA raises the error flag, stops,
+// waits for its issued MMAs and frees TMEM.
+#include "psf_internal.cuh"
+#include "tc_ptx.cuh"
+
+#include <cuda.h>
+
+namespace psf {
+namespace {
+using namespace tc;
+
+constexpr int kKrStages = 4;
+constexpr int kKrIn = 16;             // uv input ring depth (stages)
+constexpr int kKrKS = 32;             // visibilities per stage
+constexpr int kKrGenWarps = 8;
+constexpr int kKrFoldWarp0 = 8;
+constexpr int kKrTmaWarp = 12;
+constexpr int kKrMmaWarp = 13;
+constexpr int kKrThreads = 14 * 32;
+constexpr int kKrFoldStages = 64;
+constexpr uint32_t kKrATile = 128 * 128;   // 128 positions x 64 K' x 2 B
+constexpr uint32_t kKrBTile = 256 * 128;   // 256 pixels x 64 K' x 2 B
+constexpr uint32_t kKrInSlot = kKrKS * 8;  // uv per stage
+constexpr uint32_t kKrSmemBytes =
+    kKrStages * (kKrATile + kKrBTile) + kKrIn * kKrInSlot + 512 + 1024;
+
+// One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (tu (n0 + r) + phi)),
+// r = 0..31, as four interleaved 8-pixel pieces in packed FP32x2 recurrences.
+template <int BF16>
+__device__ __forceinline__ void gen_run32(uint8_t *base, const uint32_t (&off8)[8], float tu, int n0, float phi) {
+    const float2 z0 = cis_turns(fmaf(tu, (float)n0, phi));
+    const float2 z1 = cis_turns(fmaf(tu, (float)(n0 + 8), phi));
+    const float2 z2 = cis_turns(fmaf(tu, (float)(n0 + 16), phi));
+    const float2 z3 = cis_turns(fmaf(tu, (float)(n0 + 24), phi));
+    const float2 st = cis_turns(tu);
+    float2 reA = make_float2(z0.x, z2.x), imA = make_float2(z0.y, z2.y);
+    float2 reB = make_float2(z1.x, z3.x), imB = make_float2(z1.y, z3.y);
+    const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t o = off8[q];
+        *reinterpret_cast<uint32_t *>(base + q * 128 + o) = pack2<BF16>(reA.x, imA.x);
+        *reinterpret_cast<uint32_t *>(base + (q + 8) * 128 + o) = pack2<BF16>(reB.x, imB.x);
+        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + o) = pack2<BF16>(reA.y, imA.y);
+        *reinterpret_cast<uint32_t *>(base + (q + 24) * 128 + o) = pack2<BF16>(reB.y, imB.y);
+        if (q < 7) {
+            const float2 tA = __fmul2_rn(imA, nsi), uA = __fmul2_rn(imA, sr);
+            const float2 tB = __fmul2_rn(imB, nsi), uB = __fmul2_rn(imB, sr);
+            imA = __ffma2_rn(reA, si, uA);
+            reA = __ffma2_rn(reA, sr, tA);
+            imB = __ffma2_rn(reB, si, uB);
+            reB = __ffma2_rn(reB, sr, tB);
+        }
+    }
+}
+
+template <int BF16>
+__global__ void __launch_bounds__(kKrThreads, 1)
+    k_psf_kr(const __grid_constant__ CUtensorMap wmap, const KrItem *__restrict__ items, const float2 *__restrict__ uv,
+             int32_t kchunk0, float cell, const int64_t *__restrict__ out_off, float *__restrict__ out, int *err) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *a_base = smem;
+    uint8_t *b_base = smem + kKrStages * kKrATile;
+    uint8_t *in_base = b_base + kKrStages * kKrBTile;
+    uint64_t *full = (uint64_t *)(in_base + kKrIn * kKrInSlot);
+    uint64_t *empty = full + kKrStages;
+    uint64_t *in_full = empty + kKrStages;
+    uint64_t *acc_full = in_full + kKrIn;
+    uint64_t *acc_empty = acc_full + 1;
+    uint64_t *done_bar = acc_empty + 1;
+    uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
+    volatile int *s_abort = (volatile int *)(s_tmem + 1);
+
+    const KrItem it = items[blockIdx.x];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nst = (it.ke - it.kb + kKrKS - 1) / kKrKS;
+    const int nfold = (nst + kKrFoldStages - 1) / kKrFoldStages;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kKrStages; ++s) {
+            mbar_init(&full[s], kKrGenWarps + 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int s = 0; s < kKrIn; ++s) mbar_init(&in_full[s], 1);
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 4);
+        mbar_init(done_bar, 1);
+        *s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == kKrMmaWarp) {
+        tmem_alloc(s_tmem, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;   // columns [0, 256): active accumulator, [256, 512): running sum
+
+    if (warp < kKrGenWarps) {
+        // ------------------------------------------------------------ pixel twiddles
+        const int half = it.N / 2;
+        const int r0 = warp * 32;                         // this warp's 32 rows (pixels) of the B tile
+        const bool active = r0 < it.npx;
+        const int q = it.q0 + r0;
+        const int jrow = q / it.N, i0 = q - jrow * it.N;   // a 32-pixel run inside one cutout row
+        uint32_t off8[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
+        for (int s_i = 0; s_i < nst; ++s_i) {
+            const int slot = s_i % kKrStages;
+            const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
+            const int islot = s_i % kKrIn;
+            bool ok = wait_bounded(&in_full[islot], (uint32_t)(s_i / kKrIn) & 1u, s_abort, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            const float2 uvk = reinterpret_cast<const float2 *>(in_base + islot * kKrInSlot)[lane];
+            if (s_i >= kKrStages) {
+                ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
+                if (!__all_sync(0xffffffffu, ok)) break;
+            }
+            if (active) {
+                const float tu = uvk.x * cell, tv = uvk.y * cell;
+                gen_run32<BF16>(b_base + slot * kKrBTile + r0 * 128, off8, tu, i0 - half, tv * (float)(jrow - half));
+            }
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[slot]);
+        }
+    } else if (warp == kKrTmaWarp) {
+        // ------------------------------------------------------------ weight tiles
+        if (lane == 0) {
+            const int x0 = 2 * (it.kb - kchunk0);
+            for (int s_i = 0; s_i < nst; ++s_i) {
+                const int slot = s_i % kKrStages;
+                const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
+                if (s_i >= kKrStages && !wait_bounded(&empty[slot], ph ^ 1u, s_abort, err)) break;
+                mbar_arrive_expect_tx(&full[slot], kKrATile);
+                tma_load_2d(a_base + slot * kKrATile, &wmap, x0 + s_i * 2 * kKrKS, it.wrow, &full[slot]);
+            }
+        }
+        __syncwarp();
+    } else if (warp == kKrMmaWarp) {
+        // ------------------------------------------------------------ MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, it.npx, BF16);
+            auto load_uv = [&](int s) {
+                const int islot = s % kKrIn;
+                mbar_arrive_expect_tx(&in_full[islot], kKrInSlot);
+                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s * kKrKS, kKrInSlot, &in_full[islot]);
+            };
+            for (int s = 0; s < kKrIn && s < nst; ++s) load_uv(s);
+            const uint32_t a0 = smem_u32(a_base), b0 = smem_u32(b_base);
+            int in_acc = 0, folds = 0;
+            for (int s_i = 0; s_i < nst; ++s_i) {
+                const int slot = s_i % kKrStages;
+                const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
+                if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
+                if (s_i + kKrIn < nst) load_uv(s_i + kKrIn);
+                if (in_acc == 0 && folds > 0 && !wait_bounded(acc_empty, (uint32_t)(folds - 1) & 1u, s_abort, err))
+                    break;
+                tc_fence_after();
+                const uint64_t ad = desc_sw128(a0 + slot * kKrATile);
+                const uint64_t bd = desc_sw128(b0 + slot * kKrBTile);
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma_f16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
+                             (in_acc > 0 || kk > 0) ? 1u : 0u);
+                umma_commit(&empty[slot]);
+                if (++in_acc == kKrFoldStages || s_i == nst - 1) {
+                    umma_commit(acc_full);
+                    ++folds;
+                    in_acc = 0;
+                }
+            }
+            umma_commit(done_bar);
+            wait_bounded(done_bar, 0, s_abort, nullptr);
+        }
+        __syncwarp();
+    } else {
+        // ------------------------------------------------------------ fold / output
+        const int qw = warp - kKrFoldWarp0;          // TMEM lane quarter
+        const int row = qw * 32 + lane;              // position row of the tile
+        const bool row_ok = row < it.npos;
+        float *dst = out + (row_ok ? out_off[it.slot0 + row] : 0) + it.q0;
+        const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16);
+        for (int f = 0; f < nfold; ++f) {
+            const bool ok = wait_bounded(acc_full, (uint32_t)f & 1u, s_abort, err);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            const bool last = (f == nfold - 1);
+            for (int c0 = 0; c0 < it.npx; c0 += 16) {
+                float v[16];
+                tmem_ld16(ta + (uint32_t)c0, v);
+                if (f > 0) {
+                    float sacc[16];
+                    tmem_ld16(ta + 256u + (uint32_t)c0, sacc);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) v[e] += sacc[e];
+                }
+                if (last) {
+                    if (row_ok) {
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) atomicAdd(dst + c0 + e, v[e]);
+                    }
+                } else {
+                    tmem_st16(ta + 256u + (uint32_t)c0, v);
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acc_empty);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == kKrMmaWarp) tmem_dealloc(tmem, 512);
+}
+
+}  // namespace
+
+cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
+                          float cell, const int64_t *out_off, float *out, int bf16, int *err, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const CUtensorMap *m = (const CUtensorMap *)wmap;
+    cudaError_t e;
+    if (bf16) {
+        e = cudaFuncSetAttribute(k_psf_kr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrSmemBytes);
+        if (e != cudaSuccess) return e;
+        k_psf_kr<1><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
+    } else {
+        e = cudaFuncSetAttribute(k_psf_kr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrSmemBytes);
+        if (e != cudaSuccess) return e;
+        k_psf_kr<0><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
+    }
+    return cudaGetLastError();
+}
+
+// 2-D tensor map over the FP16/BF16 weight buffer: dim0 = pitch (2 KC) elements,
+// dim1 = rows; box 64 x 128 elements (one 128-byte-swizzled stage of 128 positions).
+int make_weight_map(void *map_out, void *w16, int bf16, int64_t pitch_elems, int64_t rows) {
+    typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+    static EncodeFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !ptr) {
+            cudaGetLastError();
+            return PSF_ECUDA;
+        }
+        fn = (EncodeFn)ptr;
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)pitch_elems, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch_elems * 2};
+    const cuuint32_t box[2] = {64, 128};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn((CUtensorMap *)map_out, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2,
+                    w16, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? PSF_OK : PSF_ECUDA;
+}
+
+int kr_smem_bytes() { return (int)kKrSmemBytes; }
+
+}  // namespace psf

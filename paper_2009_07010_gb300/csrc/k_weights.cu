@@ -12,6 +12,9 @@
 // accumulates a 4 x 4 pixel block of Re(c a) with two FMAs per term.  Sums are
 // kept short in FP32 (one chunk) and folded into a compensated (Kahan) FP32 total,
 // and split-K partials are added in float64, so the path meets 1e-6 relative.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
 #include "decorr.cuh"
 
 namespace psf {
@@ -38,6 +41,68 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
     if (npos <= 0 || kn <= 0) return cudaSuccess;
     dim3 grid((kn + 255) / 256, npos);
     k_weights<<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
+    return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- FP16/BF16 weights
+// Weights of a position chunk for the batched tensor-core contraction: row r holds
+// position slot_of_row[r] (zeros for padding rows, slot < 0) as (Re w, -Im w) pairs
+// at column pair (k - kc0); columns at or beyond kcn are zero.
+template <int BF16>
+__global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_t flags,
+                                                   const float4 *__restrict__ pos,
+                                                   const int32_t *__restrict__ slot_of_row, int32_t kc0,
+                                                   int32_t kcn, int64_t kpitch, uint32_t *__restrict__ w16) {
+    const int row = blockIdx.y;
+    const int32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
+    if (kk >= kpitch) return;
+    const int slot = slot_of_row[row];
+    float2 w = make_float2(0.f, 0.f);
+    if (slot >= 0 && kk < kcn) {
+        const int32_t k = kc0 + kk;
+        const int bin = k / o.nout;
+        const int r = k - bin * o.nout;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float2 D = decorr<false>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
+        const float Wk = o.W[k];
+        w = make_float2(Wk * D.x, Wk * D.y);
+    }
+    uint32_t packed;
+    if (BF16) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(w.x, -w.y);
+        packed = *reinterpret_cast<uint32_t *>(&h);
+    } else {
+        __half2 h = __floats2half2_rn(w.x, -w.y);
+        packed = *reinterpret_cast<uint32_t *>(&h);
+    }
+    w16[(int64_t)row * kpitch + kk] = packed;
+}
+
+cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const float4 *pos,
+                             const int32_t *slot_of_row, int rows, int32_t kc0, int32_t kcn, int64_t kpitch,
+                             int bf16, void *w16, cudaStream_t st) {
+    if (rows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((kpitch + 255) / 256), rows);
+    if (bf16)
+        k_weights16<1><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kpitch, (uint32_t *)w16);
+    else
+        k_weights16<0><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kpitch, (uint32_t *)w16);
+    return cudaGetLastError();
+}
+
+// Zero the listed cutouts (outputs that are accumulated with atomics).
+__global__ void __launch_bounds__(256) k_zero_cutouts(float *__restrict__ out, const int64_t *__restrict__ offs,
+                                                      const int32_t *__restrict__ npix) {
+    const int p = blockIdx.y;
+    const int64_t n2 = (int64_t)npix[p] * npix[p];
+    float *dst = out + offs[p];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x)
+        dst[q] = 0.f;
+}
+
+cudaError_t launch_zero_cutouts(float *out, const int64_t *offs, const int32_t *npix, int npos, cudaStream_t st) {
+    if (npos <= 0) return cudaSuccess;
+    k_zero_cutouts<<<dim3(16, npos), 256, 0, st>>>(out, offs, npix);
     return cudaGetLastError();
 }
 

@@ -80,6 +80,11 @@ int cuda_status(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Storage for a CUtensorMap (128 bytes, 64-byte aligned) without including cuda.h here.
+struct alignas(64) CUtensorMapStub {
+    unsigned char bytes[128];
+};
+
 }  // namespace
 
 struct psf_plan_s {
@@ -96,6 +101,7 @@ struct psf_plan_s {
     DevBuf meta;         // positions, sizes, offsets, tiles
     DevBuf wbuf;         // weights of a chunk of positions
     DevBuf partial;      // split-K partial cutouts
+    DevBuf w16;          // FP16/BF16 weights of the batched path
     HostPinned hmeta;
     cudaEvent_t meta_done = nullptr;   // staging buffer reusable once this fires
     // diagnostic timing (psf_profile_*)
@@ -405,14 +411,138 @@ int upload_meta(psf_plan_s *p, const void *src, size_t bytes, cudaStream_t st) {
 }
 
 constexpr size_t kWeightBudget = size_t(4) << 30;   // weights of one position chunk (bytes)
+constexpr size_t kW16Budget = size_t(4) << 30;      // FP16 weights of one batched chunk (bytes)
+constexpr int kKrMinGroup = 32;                     // positions of one size for the batched form
+
+// Batched tensor-core path for one group of positions with the same cutout size N
+// (N a multiple of 32, <= 256): weights of the group for a chunk of visibilities are
+// written as FP16/BF16 pairs, then the Khatri-Rao kernel accumulates every
+// (128-position tile, 256-pixel tile, visibility range) item into the zeroed output.
+int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int> &idx, int N, float *out,
+           cudaStream_t st) {
+    const int np = (int)idx.size();
+    const int ntile = (np + 127) / 128;
+    const int rows = ntile * 128;
+    const int64_t K = p->nvis;
+    const int bf16 = p->opts.prec == PSF_TC_BF16;
+    int64_t KC = (int64_t)(kW16Budget / ((size_t)rows * 4)) / 32 * 32;
+    KC = std::max<int64_t>(32, std::min<int64_t>(KC, (K + 31) / 32 * 32));
+    const int64_t nchunk = (K + KC - 1) / KC;
+    const int ptiles = N * N / 256;
+    // positions, per-row slots, per-slot output offsets (uploaded once), items per chunk
+    std::vector<float4> pos(np);
+    std::vector<int32_t> slot_of_row(rows, -1), npix(np, N);
+    std::vector<int64_t> outo(np);
+    for (int i = 0; i < np; ++i) {
+        pos[i] = h.pos[idx[i]];
+        slot_of_row[i] = i;
+        outo[i] = h.out_off[idx[i]];
+    }
+    PSF_TRY(p->w16.reserve((size_t)rows * KC * 4));
+    CUtensorMapStub wmap;
+    int s = make_weight_map(&wmap, p->w16.p, bf16, 2 * KC, rows);
+    if (s) return s;
+    const int64_t nbase = (int64_t)ntile * ptiles;
+    for (int64_t c = 0; c < nchunk; ++c) {
+        const int64_t kc0 = c * KC, kcn = std::min<int64_t>(KC, K - kc0);
+        const int64_t nst = (kcn + 31) / 32;
+        int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((2 * p->nsm + nbase - 1) / nbase, nst / 64));
+        const int64_t sper = (nst + nsplit - 1) / nsplit;
+        nsplit = (nst + sper - 1) / sper;
+        std::vector<KrItem> items;
+        items.reserve(nbase * nsplit);
+        for (int t = 0; t < ntile; ++t)
+            for (int64_t sp = 0; sp < nsplit; ++sp)
+                for (int q = 0; q < ptiles; ++q) {
+                    KrItem it;
+                    it.wrow = t * 128;
+                    it.npos = std::min(128, np - t * 128);
+                    it.slot0 = t * 128;
+                    it.N = N;
+                    it.q0 = q * 256;
+                    it.npx = 256;
+                    it.kb = (int32_t)(kc0 + sp * sper * 32);
+                    it.ke = (int32_t)std::min<int64_t>(kc0 + kcn, kc0 + (sp + 1) * sper * 32);
+                    items.push_back(it);
+                }
+        const size_t off_pos = 0;
+        const size_t off_slot = align_up(off_pos + np * sizeof(float4), 16);
+        const size_t off_outo = align_up(off_slot + rows * sizeof(int32_t), 16);
+        const size_t off_npix = align_up(off_outo + np * sizeof(int64_t), 16);
+        const size_t off_items = align_up(off_npix + np * sizeof(int32_t), 16);
+        const size_t bytes = align_up(off_items + items.size() * sizeof(KrItem), 16);
+        std::vector<char> blob(bytes, 0);
+        std::memcpy(blob.data() + off_pos, pos.data(), np * sizeof(float4));
+        std::memcpy(blob.data() + off_slot, slot_of_row.data(), rows * sizeof(int32_t));
+        std::memcpy(blob.data() + off_outo, outo.data(), np * sizeof(int64_t));
+        std::memcpy(blob.data() + off_npix, npix.data(), np * sizeof(int32_t));
+        std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(KrItem));
+        if ((s = upload_meta(p, blob.data(), bytes, st))) return s;
+        char *dm = (char *)p->meta.p;
+        if (c == 0) {
+            PSF_TRY(launch_zero_cutouts(out, (const int64_t *)(dm + off_outo), (const int32_t *)(dm + off_npix), np, st));
+            p->n_kernels++;
+        }
+        PSF_TRY(launch_weights16(p->d, method, p->opts.flags, (const float4 *)(dm + off_pos),
+                                 (const int32_t *)(dm + off_slot), rows, (int32_t)kc0, (int32_t)kcn, KC, bf16,
+                                 p->w16.p, st));
+        p->n_kernels++;
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        if (p->prof) {
+            if (p->prof_used == p->prof_ev.size()) {
+                cudaEvent_t a, e2;
+                PSF_TRY(cudaEventCreate(&a));
+                PSF_TRY(cudaEventCreate(&e2));
+                p->prof_ev.emplace_back(a, e2);
+            }
+            ev1 = p->prof_ev[p->prof_used].first;
+            ev2 = p->prof_ev[p->prof_used].second;
+            p->prof_used++;
+            PSF_TRY(cudaEventRecord(ev1, st));
+        }
+        PSF_TRY(launch_psf_kr(&wmap, (const KrItem *)(dm + off_items), (int)items.size(), p->d.uv, (int32_t)kc0,
+                              (float)h.cell, (const int64_t *)(dm + off_outo), out, bf16, (int *)p->err.p, st));
+        if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+        p->n_contract++;
+        p->n_kernels++;
+    }
+    return PSF_OK;
+}
 
 int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st) {
     if (!p || !out) return PSF_EINVAL;
     const bool tc = p->opts.prec != PSF_FP32;
-    BatchHost h;
-    int s = prepare_batch(p, b, h, tc ? 256 : 4096);
-    if (s || h.npos == 0) return s;
+    BatchHost hall;
+    int s = prepare_batch(p, b, hall, tc ? 256 : 4096);
+    if (s || hall.npos == 0) return s;
     const int64_t K = p->nvis;
+    // Batched tensor-core form for large groups of one eligible size; the rest goes
+    // through the per-cutout form below.
+    BatchHost h;
+    h.cell = hall.cell;
+    if (tc && p->opts.algo == PSF_ALGO_AUTO) {
+        std::vector<std::vector<int>> groups(257);
+        for (int i = 0; i < hall.npos; ++i) {
+            const int N = hall.npix[i];
+            if (N % 32 == 0 && N >= 32 && N <= 256) groups[N].push_back(i);
+        }
+        std::vector<char> done(hall.npos, 0);
+        for (int N = 32; N <= 256; N += 32) {
+            if ((int)groups[N].size() < kKrMinGroup) continue;
+            if ((s = run_kr(p, method, hall, groups[N], N, out, st))) return s;
+            for (int i : groups[N]) done[i] = 1;
+        }
+        for (int i = 0; i < hall.npos; ++i)
+            if (!done[i]) {
+                h.pos.push_back(hall.pos[i]);
+                h.npix.push_back(hall.npix[i]);
+                h.out_off.push_back(hall.out_off[i]);
+            }
+        h.npos = (int)h.pos.size();
+        if (h.npos == 0) return PSF_OK;
+    } else {
+        h = hall;
+    }
     const int chunk = (int)std::max<int64_t>(
         1, std::min<int64_t>(std::min<int64_t>(h.npos, 32768), kWeightBudget / (K * 8)));
 

@@ -79,6 +79,25 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
                           int64_t split_stride, int *err_flag, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
 
+// ---- batched tcgen05 contraction (k_kr.cu) ---------------------------------
+struct KrItem {
+    int32_t wrow;     // first row of the 128-position tile in the weight buffer
+    int32_t npos;     // valid positions of the tile (<= 128)
+    int32_t slot0;    // batch index of the tile's first position
+    int32_t N;        // cutout size (multiple of 32, <= 256)
+    int32_t q0;       // first pixel (row-major) of the 256-pixel tile
+    int32_t npx;      // pixels of the tile (256)
+    int32_t kb, ke;   // visibility range, kb - chunk start a multiple of 32
+};
+cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
+                          float cell, const int64_t *out_off, float *out, int bf16, int *err, cudaStream_t st);
+int make_weight_map(void *map_out, void *w16, int bf16, int64_t pitch_elems, int64_t rows);
+int kr_smem_bytes();
+cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const float4 *pos,
+                             const int32_t *slot_of_row, int rows, int32_t kc0, int32_t kcn, int64_t kpitch,
+                             int bf16, void *w16, cudaStream_t st);
+cudaError_t launch_zero_cutouts(float *out, const int64_t *offs, const int32_t *npix, int npos, cudaStream_t st);
+
 // Read-only views of a plan (plan.cu).
 const DevObs *plan_devobs(psf_plan_t p);
 uint32_t plan_flags(psf_plan_t p);
