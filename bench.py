@@ -183,6 +183,60 @@ def cpu_baseline_sample(obs, batch):
                       f"({dt:.1f} s incl. the oracle's binning and decorrelation pass)"}
 
 
+def measure_batched(psf, prec, steps=2):
+    """Batched form on the differentiation workload: 256 positions, 64 x 64 cutouts,
+    the baseline-dependent-averaging observation (~1.45e7 visibilities); forward
+    (exact + uv + img) and the adjoint of the exact method."""
+    import torch
+    obs = obsgen.config3_obs()
+    bg = obsgen.config4_batch()
+    batch = psf.Batch.from_obsgen(bg)
+    K = obs.nvis()
+    terms = 3 * K * bg.total_pixels()
+    peaks, src = load_peaks()
+    plan = psf.Plan(obs, prec=prec)
+    out = torch.empty(batch.total(), dtype=torch.float32, device="cuda")
+
+    def step():
+        for m in ("exact", "uv", "img"):
+            plan.forward(m, batch, out=out)
+    step()
+    torch.cuda.synchronize()
+    plan.profile_read()
+    plan.profile_enable(True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kms, nkc, nk = plan.profile_read()
+    plan.profile_enable(False)
+    per_launch_flops = 4.0 * K * bg.total_pixels() * steps * 3 / max(nkc, 1)
+    ach = per_launch_flops / (kms / max(nkc, 1) * 1e-3) / 1e12
+    # adjoint of the exact method (FP32 CUDA cores)
+    R = torch.randn(batch.total(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+    plan.adjoint("exact", batch, R)
+    torch.cuda.synchronize()
+    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record()
+    plan.adjoint("exact", batch, R)
+    a1.record()
+    torch.cuda.synchronize()
+    ams = a0.elapsed_time(a1)
+    st = plan.sync_status()
+    plan.close()
+    if st != 0:
+        raise RuntimeError("device-side wait timed out in the batched measurement")
+    return {"workload": "meerkat64_2h_8ch_bda_256pos_64px", "nvis": K, "positions": bg.npos, "npix": 64,
+            "value": terms / (ms * 1e-3), "unit": "terms/s", "ms_per_step": ms, "methods": ["exact", "uv", "img"],
+            "kernel": "k_psf_kr (tcgen05 batched contraction)", "kernel_ms_per_launch": kms / max(nkc, 1),
+            "kernel_launches": nkc, "kernel_tflops": ach, "kernel_frac_of_peak": ach / peaks["bf16_tflops"],
+            "peak_source": src,
+            "adjoint_exact": {"ms": ams, "terms_per_s": K * bg.total_pixels() / (ams * 1e-3), "precision": "fp32"}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -193,6 +247,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures)")
@@ -298,6 +353,8 @@ def main():
         e2e = {"value": world * terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "ms_per_step": dt * 1e3}
 
+    batched = None if args.no_batched else measure_batched(psf, args.prec)
+
     if rank == 0:
         peaks, src = load_peaks()
         peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
@@ -319,7 +376,7 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
