@@ -32,11 +32,12 @@ using namespace tc;
 constexpr int kKrStages = 4;
 constexpr int kKrIn = 16;             // uv input ring depth (stages)
 constexpr int kKrKS = 32;             // visibilities per stage
-constexpr int kKrGenWarps = 8;
-constexpr int kKrFoldWarp0 = 8;
-constexpr int kKrTmaWarp = 12;
-constexpr int kKrMmaWarp = 13;
-constexpr int kKrThreads = 14 * 32;
+constexpr int kKrGenWarps = 16;       // two groups of 8 on alternate stages
+constexpr int kKrGroupWarps = 8;
+constexpr int kKrFoldWarp0 = 16;
+constexpr int kKrTmaWarp = 20;
+constexpr int kKrMmaWarp = 21;
+constexpr int kKrThreads = 22 * 32;
 constexpr int kKrFoldStages = 64;
 constexpr uint32_t kKrATile = 128 * 128;   // 128 positions x 64 K' x 2 B
 constexpr uint32_t kKrBTile = 256 * 128;   // 256 pixels x 64 K' x 2 B
@@ -47,7 +48,7 @@ constexpr uint32_t kKrSmemBytes =
 // One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (tu (n0 + r) + phi)),
 // r = 0..31, as four interleaved 8-pixel pieces in packed FP32x2 recurrences.
 template <int BF16>
-__device__ __forceinline__ void gen_run32(uint8_t *base, const uint32_t (&off8)[8], float tu, int n0, float phi) {
+__device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float tu, int n0, float phi) {
     const float2 z0 = cis_turns(fmaf(tu, (float)n0, phi));
     const float2 z1 = cis_turns(fmaf(tu, (float)(n0 + 8), phi));
     const float2 z2 = cis_turns(fmaf(tu, (float)(n0 + 16), phi));
@@ -58,11 +59,8 @@ __device__ __forceinline__ void gen_run32(uint8_t *base, const uint32_t (&off8)[
     const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const uint32_t o = off8[q];
-        *reinterpret_cast<uint32_t *>(base + q * 128 + o) = pack2<BF16>(reA.x, imA.x);
-        *reinterpret_cast<uint32_t *>(base + (q + 8) * 128 + o) = pack2<BF16>(reB.x, imB.x);
-        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + o) = pack2<BF16>(reA.y, imA.y);
-        *reinterpret_cast<uint32_t *>(base + (q + 24) * 128 + o) = pack2<BF16>(reB.y, imB.y);
+        stmatrix_x4(base + off[q], pack2<BF16>(reA.x, imA.x), pack2<BF16>(reB.x, imB.x), pack2<BF16>(reA.y, imA.y),
+                    pack2<BF16>(reB.y, imB.y));
         if (q < 7) {
             const float2 tA = __fmul2_rn(imA, nsi), uA = __fmul2_rn(imA, sr);
             const float2 tB = __fmul2_rn(imB, nsi), uB = __fmul2_rn(imB, sr);
@@ -99,7 +97,7 @@ __global__ void __launch_bounds__(kKrThreads, 1)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kKrStages; ++s) {
-            mbar_init(&full[s], kKrGenWarps + 1);
+            mbar_init(&full[s], kKrGroupWarps + 1);
             mbar_init(&empty[s], 1);
         }
         for (int s = 0; s < kKrIn; ++s) mbar_init(&in_full[s], 1);
@@ -121,14 +119,14 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     if (warp < kKrGenWarps) {
         // ------------------------------------------------------------ pixel twiddles
         const int half = it.N / 2;
-        const int r0 = warp * 32;                         // this warp's 32 rows (pixels) of the B tile
+        const int grp = warp / kKrGroupWarps, gw = warp % kKrGroupWarps;
+        const int r0 = gw * 32;                           // this warp's 32 rows (pixels) of the B tile
         const bool active = r0 < it.npx;
         const int q = it.q0 + r0;
         const int jrow = q / it.N, i0 = q - jrow * it.N;   // a 32-pixel run inside one cutout row
         uint32_t off8[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
-        for (int s_i = 0; s_i < nst; ++s_i) {
+        stmatrix_offsets(lane, off8);
+        for (int s_i = grp; s_i < nst; s_i += 2) {
             const int slot = s_i % kKrStages;
             const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
             const int islot = s_i % kKrIn;
@@ -141,7 +139,8 @@ __global__ void __launch_bounds__(kKrThreads, 1)
             }
             if (active) {
                 const float tu = uvk.x * cell, tv = uvk.y * cell;
-                gen_run32<BF16>(b_base + slot * kKrBTile + r0 * 128, off8, tu, i0 - half, tv * (float)(jrow - half));
+                gen_run32<BF16>(smem_u32(b_base + slot * kKrBTile + r0 * 128), off8, tu, i0 - half,
+                                tv * (float)(jrow - half));
             }
             fence_proxy_async_smem();
             __syncwarp();

@@ -45,9 +45,10 @@ constexpr int kATileBytes = 128 * 128;
 // value(r) = [w] exp(2 pi i theta (n0 + r)), written as an FP16/BF16 (re, im) pair at
 // the lane's K-major swizzled slot.  The chain runs as four interleaved 8-row pieces
 // (seeds at r = 0, 8, 16, 24) held in two packed FP32x2 pairs, so each step is two
-// independent packed complex multiplications.
+// independent packed complex multiplications, and the four rows of a step leave in
+// one stmatrix.
 template <int BF16>
-__device__ __forceinline__ void gen_chain32(uint8_t *base, const uint32_t (&off8)[8], float theta, int n0,
+__device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0,
                                             float2 wk, bool weighted) {
     float2 z0 = cis_turns(theta * (float)n0);
     float2 z1 = cis_turns(theta * (float)(n0 + 8));
@@ -65,11 +66,9 @@ __device__ __forceinline__ void gen_chain32(uint8_t *base, const uint32_t (&off8
     const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-        const uint32_t o = off8[q];
-        *reinterpret_cast<uint32_t *>(base + q * 128 + o) = pack2<BF16>(reA.x, imA.x);
-        *reinterpret_cast<uint32_t *>(base + (q + 8) * 128 + o) = pack2<BF16>(reB.x, imB.x);
-        *reinterpret_cast<uint32_t *>(base + (q + 16) * 128 + o) = pack2<BF16>(reA.y, imA.y);
-        *reinterpret_cast<uint32_t *>(base + (q + 24) * 128 + o) = pack2<BF16>(reB.y, imB.y);
+        // rows q, q + 8, q + 16, q + 24 in one stmatrix
+        stmatrix_x4(base + off[q], pack2<BF16>(reA.x, imA.x), pack2<BF16>(reB.x, imB.x), pack2<BF16>(reA.y, imA.y),
+                    pack2<BF16>(reB.y, imB.y));
         if (q < 7) {
             const float2 tA = __fmul2_rn(imA, nsi), uA = __fmul2_rn(imA, sr);
             const float2 tB = __fmul2_rn(imB, nsi), uB = __fmul2_rn(imB, sr);
@@ -158,8 +157,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nA = 4, nB = ncols / 32;   // 32-row chains of the A (128 rows) and B tiles
         const int half = it.N / 2;
         uint32_t off8[8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) off8[c] = ((uint32_t)(((lane >> 2) ^ c)) << 4) + ((uint32_t)(lane & 3) << 2);
+        stmatrix_offsets(lane, off8);
         for (int s_i = grp; s_i < nst; s_i += 2) {
             const int slot = s_i % kStages;
             const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
@@ -173,8 +171,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            uint8_t *a_tile = smem + L.a_off + slot * kATileBytes;
-            uint8_t *b_tile = smem + L.b_off + slot * bt_stride;
+            const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kATileBytes);
+            const uint32_t b_tile = smem_u32(smem + L.b_off + slot * bt_stride);
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
                 if (ch < nA)   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
                     gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk, true);

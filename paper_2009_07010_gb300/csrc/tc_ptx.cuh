@@ -191,6 +191,27 @@ static __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
 }
 
 
+// Four 8x8 b16 matrices from registers to shared memory.  Lane t holds, per matrix,
+// the 32-bit pair at matrix row t/4, columns 2(t%4), 2(t%4)+1; lanes 8m..8m+7 give
+// the 16-byte row addresses of matrix m.  With one K-major 128-byte operand row per
+// matrix, lane t's pair is K' elements (2t, 2t+1) of that row: one instruction
+// stores four operand rows of one 32-visibility stage.
+static __device__ __forceinline__ void stmatrix_x4(uint32_t saddr, uint32_t v0, uint32_t v1, uint32_t v2,
+                                                   uint32_t v3) {
+    asm volatile("stmatrix.sync.aligned.m8n8.x4.shared.b16 [%0], {%1, %2, %3, %4};" ::"r"(saddr), "r"(v0), "r"(v1),
+                 "r"(v2), "r"(v3)
+                 : "memory");
+}
+
+// Per-lane stmatrix addresses for the four rows q, q+8, q+16, q+24 (q = 0..7) of a
+// 32-row block of a K-major 128-byte-swizzled tile: lane t addresses matrix t/8
+// (row q + 8 (t/8)), 16-byte chunk t%8, swizzled by XOR with the row index mod 8 (= q).
+static __device__ __forceinline__ void stmatrix_offsets(int lane, uint32_t (&off)[8]) {
+    const uint32_t m = (uint32_t)lane >> 3, a = (uint32_t)lane & 7u;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) off[q] = (uint32_t)q * 128u + m * 1024u + ((a ^ (uint32_t)q) << 4);
+}
+
 // 2-D tiled TMA load of one box into shared memory, completing on `bar`.
 static __device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
     asm volatile(
