@@ -248,13 +248,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c4"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
-                         "(a quarter of the visibilities, for profiler captures)")
+                         "(a quarter of the visibilities, for profiler captures); c4: only the batched "
+                         "256 x 64^2 measurement (profiler captures of the batched kernel)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "c4":
+        import torch
+        import paper_2009_07010_gb300 as psf
+        psf.build_library()
+        torch.cuda.set_device(local)
+        print(json.dumps(measure_batched(psf, args.prec, steps=args.steps)), flush=True)
+        return 0
 
     import torch
     import paper_2009_07010_gb300 as psf

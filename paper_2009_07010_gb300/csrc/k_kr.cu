@@ -45,29 +45,37 @@ constexpr uint32_t kKrInSlot = kKrKS * 8;  // uv per stage
 constexpr uint32_t kKrSmemBytes =
     kKrStages * (kKrATile + kKrBTile) + kKrIn * kKrInSlot + 512 + 1024;
 
-// One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (tu (n0 + r) + phi)),
-// r = 0..31, as four interleaved 8-pixel pieces in packed FP32x2 recurrences.
+// One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (theta (n0 + r) + phi)),
+// r = 0..31, as eight interleaved 4-pixel pieces in packed FP32x2 recurrences.
 template <int BF16>
-__device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float tu, int n0, float phi) {
-    const float2 z0 = cis_turns(fmaf(tu, (float)n0, phi));
-    const float2 z1 = cis_turns(fmaf(tu, (float)(n0 + 8), phi));
-    const float2 z2 = cis_turns(fmaf(tu, (float)(n0 + 16), phi));
-    const float2 z3 = cis_turns(fmaf(tu, (float)(n0 + 24), phi));
-    const float2 st = cis_turns(tu);
-    float2 reA = make_float2(z0.x, z2.x), imA = make_float2(z0.y, z2.y);
-    float2 reB = make_float2(z1.x, z3.x), imB = make_float2(z1.y, z3.y);
+__device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float phi) {
+    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3
+    float2 z[8];
+#pragma unroll
+    for (int pc = 0; pc < 8; ++pc) z[pc] = cis_turns(fmaf(theta, (float)(n0 + 4 * pc), phi));
+    const float2 st = cis_turns(theta);
+
+    // packed pairs: P0 = rows (q, q+16), P1 = (q+8, q+24), P2 = (q+4, q+20), P3 = (q+12, q+28)
+    float2 re[4], im[4];
+    re[0] = make_float2(z[0].x, z[4].x); im[0] = make_float2(z[0].y, z[4].y);
+    re[1] = make_float2(z[2].x, z[6].x); im[1] = make_float2(z[2].y, z[6].y);
+    re[2] = make_float2(z[1].x, z[5].x); im[2] = make_float2(z[1].y, z[5].y);
+    re[3] = make_float2(z[3].x, z[7].x); im[3] = make_float2(z[3].y, z[7].y);
     const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        stmatrix_x4(base + off[q], pack2<BF16>(reA.x, imA.x), pack2<BF16>(reB.x, imB.x), pack2<BF16>(reA.y, imA.y),
-                    pack2<BF16>(reB.y, imB.y));
-        if (q < 7) {
-            const float2 tA = __fmul2_rn(imA, nsi), uA = __fmul2_rn(imA, sr);
-            const float2 tB = __fmul2_rn(imB, nsi), uB = __fmul2_rn(imB, sr);
-            imA = __ffma2_rn(reA, si, uA);
-            reA = __ffma2_rn(reA, sr, tA);
-            imB = __ffma2_rn(reB, si, uB);
-            reB = __ffma2_rn(reB, sr, tB);
+    for (int q = 0; q < 4; ++q) {
+        // rows q, q+8, q+16, q+24 and rows q+4, q+12, q+20, q+28
+        stmatrix_x4(base + off[q], pack2<BF16>(re[0].x, im[0].x), pack2<BF16>(re[1].x, im[1].x),
+                    pack2<BF16>(re[0].y, im[0].y), pack2<BF16>(re[1].y, im[1].y));
+        stmatrix_x4(base + off[q + 4], pack2<BF16>(re[2].x, im[2].x), pack2<BF16>(re[3].x, im[3].x),
+                    pack2<BF16>(re[2].y, im[2].y), pack2<BF16>(re[3].y, im[3].y));
+        if (q < 3) {
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const float2 t = __fmul2_rn(im[pp], nsi), u = __fmul2_rn(im[pp], sr);
+                im[pp] = __ffma2_rn(re[pp], si, u);
+                re[pp] = __ffma2_rn(re[pp], sr, t);
+            }
         }
     }
 }
