@@ -202,6 +202,14 @@ const char *psf_strerror(int status);
  * d_dev [128][n] (device).  n in {16, 32, ..., 256}.  Synchronous. */
 int psf_selftest_umma(const void *a_dev, const void *b_dev, float *d_dev, int n);
 
+/* Diagnostic of the bounded device-side waits every tensor-core kernel uses: one CTA
+ * waits on a barrier that nothing completes, with a wall-clock limit of limit_ms
+ * milliseconds (1..10000); the wait gives up, the kernel raises its error flag and
+ * returns.  Returns PSF_ETIMEOUT when the wait ran out (the expected outcome), PSF_OK
+ * if it completed, PSF_EINVAL for a bad limit, PSF_ECUDA on a CUDA error.  The
+ * device context stays usable.  Synchronous. */
+int psf_selftest_timeout(int limit_ms);
+
 #ifdef __cplusplus
 }
 #endif

@@ -446,7 +446,21 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
     for (int64_t c = 0; c < nchunk; ++c) {
         const int64_t kc0 = c * KC, kcn = std::min<int64_t>(KC, K - kc0);
         const int64_t nst = (kcn + 31) / 32;
-        int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((2 * p->nsm + nbase - 1) / nbase, nst / 64));
+        // visibility splits: the number of CTAs (tiles x splits, one CTA per SM) should
+        // fill whole waves; among split counts giving >= 2 waves (and >= 64 stages per
+        // split) take the one with the best last-wave occupancy
+        int64_t nsplit = 1;
+        {
+            const int64_t maxs = std::max<int64_t>(1, nst / 64);
+            double best = -1.0;
+            for (int64_t cand = 1; cand <= std::min<int64_t>(maxs, 256); ++cand) {
+                const int64_t ctas = nbase * cand;
+                const int64_t waves = (ctas + p->nsm - 1) / p->nsm;
+                const double eff = (double)ctas / (double)(waves * p->nsm);
+                const double score = eff - (waves < 2 && cand < maxs ? 0.5 : 0.0) - 0.002 * (double)cand;
+                if (score > best) { best = score; nsplit = cand; }
+            }
+        }
         const int64_t sper = (nst + nsplit - 1) / nsplit;
         nsplit = (nst + sper - 1) / sper;
         std::vector<KrItem> items;
