@@ -20,7 +20,7 @@ EXACT, UV, IMG = 0, 1, 2
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
            "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
-           "psf_strerror", "psf_selftest_umma", "psf_exact_noalloc"]
+           "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
 
 
 class PsfError(RuntimeError):
@@ -89,6 +89,8 @@ def lib(auto_build: bool = False):
             L.psf_plan_destroy.restype = None
             L.psf_strerror.argtypes = [I]
             L.psf_strerror.restype = ctypes.c_char_p
+            L.psf_selftest_timeout.argtypes = [I]
+            L.psf_selftest_timeout.restype = I
             L.psf_selftest_umma.argtypes = [P, P, P, I]
             L.psf_selftest_umma.restype = I
             _LIB = L

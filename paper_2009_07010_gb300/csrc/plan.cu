@@ -780,6 +780,11 @@ uint32_t plan_flags(psf_plan_t p) { return p ? p->opts.flags : 0u; }
 
 extern "C" {
 
+int psf_selftest_timeout(int limit_ms) {
+    if (limit_ms < 1 || limit_ms > 10000) return PSF_EINVAL;
+    return selftest_timeout(limit_ms);
+}
+
 int psf_selftest_umma(const void *a, const void *b, float *d, int n) {
     if (!a || !b || !d || n < 16 || n > 256 || (n % 16)) return PSF_EINVAL;
     return selftest_umma(a, b, d, n);
