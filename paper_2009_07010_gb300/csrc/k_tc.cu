@@ -338,7 +338,43 @@ __global__ void __launch_bounds__(128, 1)
     if (warp == 0) tmem_dealloc(tmem, cols);
 }
 
+// A wait that nothing completes: the bounded-wait path with a caller-given limit.
+__global__ void k_wait_timeout(unsigned long long limit_ns, int *err) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned long long t0 = globaltimer();
+        for (;;) {
+            if (mbar_try_wait(&bar, 0, 100000u)) return;   // never completes
+            if (globaltimer() - t0 > limit_ns) {
+                atomicExch(err, 1);
+                return;
+            }
+        }
+    }
+}
+
 }  // namespace
+
+int selftest_timeout(int limit_ms) {
+    int *err = nullptr;
+    if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) { cudaGetLastError(); return PSF_ENOMEM; }
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_timeout<<<1, 32>>>((unsigned long long)limit_ms * 1000000ull, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    int flag = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) { cudaGetLastError(); return PSF_ECUDA; }
+    return flag ? PSF_ETIMEOUT : PSF_OK;
+}
 
 template <int BF16, int S>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,

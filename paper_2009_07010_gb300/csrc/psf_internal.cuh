@@ -78,6 +78,7 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
                           int nitems, int ncols_max, int bf16, float cell, float *partial,
                           int64_t split_stride, int *err_flag, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
+int selftest_timeout(int limit_ms);
 
 // ---- batched tcgen05 contraction (k_kr.cu) ---------------------------------
 struct KrItem {
