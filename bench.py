@@ -183,13 +183,15 @@ def cpu_baseline_sample(obs, batch):
                       f"({dt:.1f} s incl. the oracle's binning and decorrelation pass)"}
 
 
-def measure_batched(psf, prec, steps=2):
-    """Batched form on the differentiation workload: 256 positions, 64 x 64 cutouts,
-    the baseline-dependent-averaging observation (~1.45e7 visibilities); forward
-    (exact + uv + img) and the adjoint of the exact method."""
+def measure_batched(psf, prec, steps=2, which="c4"):
+    """Batched form on the differentiation workload (c4: 256 positions, 64 x 64
+    cutouts) or the batched-positions workload (c3: 4096 positions within 2 degrees,
+    sizes drawn from 32..256); both on the baseline-dependent-averaging observation
+    (13 710 280 visibilities): forward (exact + uv + img) and, for c4, the adjoint of
+    the exact method."""
     import torch
     obs = obsgen.config3_obs()
-    bg = obsgen.config4_batch()
+    bg = obsgen.config4_batch() if which == "c4" else obsgen.config3_batch()
     batch = psf.Batch.from_obsgen(bg)
     K = obs.nvis()
     terms = 3 * K * bg.total_pixels()
@@ -215,26 +217,87 @@ def measure_batched(psf, prec, steps=2):
     plan.profile_enable(False)
     per_launch_flops = 4.0 * K * bg.total_pixels() * steps * 3 / max(nkc, 1)
     ach = per_launch_flops / (kms / max(nkc, 1) * 1e-3) / 1e12
-    # adjoint of the exact method (FP32 CUDA cores)
-    R = torch.randn(batch.total(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
-    plan.adjoint("exact", batch, R)
-    torch.cuda.synchronize()
-    a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a0.record()
-    plan.adjoint("exact", batch, R)
-    a1.record()
-    torch.cuda.synchronize()
-    ams = a0.elapsed_time(a1)
+    adj = None
+    if which == "c4":   # adjoint of the exact method (FP32 CUDA cores)
+        R = torch.randn(batch.total(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
+        plan.adjoint("exact", batch, R)
+        torch.cuda.synchronize()
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record()
+        plan.adjoint("exact", batch, R)
+        a1.record()
+        torch.cuda.synchronize()
+        ams = a0.elapsed_time(a1)
+        adj = {"ms": ams, "terms_per_s": K * bg.total_pixels() / (ams * 1e-3), "precision": "fp32"}
     st = plan.sync_status()
     plan.close()
     if st != 0:
         raise RuntimeError("device-side wait timed out in the batched measurement")
-    return {"workload": "meerkat64_2h_8ch_bda_256pos_64px", "nvis": K, "positions": bg.npos, "npix": 64,
+    name = "meerkat64_2h_8ch_bda_256pos_64px" if which == "c4" else "meerkat64_2h_8ch_bda_4096pos_32to256px"
+    return {"workload": name, "nvis": K, "positions": bg.npos, "npix": sorted(set(int(x) for x in bg.npix)),
             "value": terms / (ms * 1e-3), "unit": "terms/s", "ms_per_step": ms, "methods": ["exact", "uv", "img"],
             "kernel": "k_psf_kr (tcgen05 batched contraction)", "kernel_ms_per_launch": kms / max(nkc, 1),
             "kernel_launches": nkc, "kernel_tflops": ach, "kernel_frac_of_peak": ach / peaks["bf16_tflops"],
             "peak_source": src,
-            "adjoint_exact": {"ms": ams, "terms_per_s": K * bg.total_pixels() / (ams * 1e-3), "precision": "fp32"}}
+            "adjoint_exact": adj}
+
+
+def measure_c5(psf, prec, nang=2, nrad=128):
+    """Approximations vs exact on the approximation workload (64-antenna 8 km array,
+    4 h at 8 s bins, 256 x 3.34375 MHz channels averaged 4:1 -> 232 243 200
+    visibilities, 64 x 64 cutouts on a radial grid out to 3 degrees): per position
+    the peak-normalised max and RMS error of Method 1 (uv) and Method 2 (img) against
+    the exact smeared PSF (tensor-core exact, itself within 1e-4 of the FP64 oracle on
+    the parity workloads), and the exact / approximation cost ratio."""
+    import torch
+    obs = obsgen.config5_obs()
+    bg = obsgen.config5_batch(nrad=nrad, nang=nang)
+    batch = psf.Batch.from_obsgen(bg)
+    K = obs.nvis()
+    plan = psf.Plan(obs, prec=prec)
+    outs, ms = {}, {}
+    for m in ("exact", "uv", "img"):
+        out = torch.empty(batch.total(), dtype=torch.float32, device="cuda")
+        plan.forward(m, batch, out=out)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        plan.forward(m, batch, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        ms[m] = e0.elapsed_time(e1)
+        outs[m] = out.cpu().numpy().astype(np.float64).reshape(bg.npos, -1)
+    st = plan.sync_status()
+    plan.close()
+    if st != 0:
+        raise RuntimeError("device-side wait timed out in the approximation workload")
+    ex = outs["exact"]
+    peak = np.max(np.abs(ex), axis=1)
+    radius_deg = np.degrees(np.arcsin(np.hypot(bg.lm[:, 0], bg.lm[:, 1])))
+    res = {}
+    for m in ("uv", "img"):
+        d = outs[m] - ex
+        emax = np.max(np.abs(d), axis=1) / peak
+        erms = np.sqrt(np.mean(d * d, axis=1)) / peak
+        by_r = {}
+        for r in np.unique(np.round(radius_deg, 4)):
+            sel = np.abs(radius_deg - r) < 1e-3
+            by_r[float(r)] = (float(emax[sel].max()), float(erms[sel].max()))
+        rs = sorted(by_r)
+        picks = [rs[int(round(x * (len(rs) - 1)))] for x in (0.0, 0.16, 0.33, 0.5, 0.83, 1.0)]
+        res[m] = {"err_max_peak_normalised": {f"{r:.3f}deg": by_r[r][0] for r in picks},
+                  "err_rms_peak_normalised": {f"{r:.3f}deg": by_r[r][1] for r in picks},
+                  "err_max_dB": {f"{r:.3f}deg": float(10 * np.log10(by_r[r][0])) for r in picks},
+                  "worst": float(emax.max())}
+    terms = K * bg.total_pixels()
+    return {"workload": "meerkat64_8km_4h_256ch_avg4_radial_64px", "nvis": K, "positions": bg.npos,
+            "positions_note": f"{nang} angles x {nrad} radii of the 128 x 128 radial grid",
+            "ms": ms, "terms_per_s": {m: terms / (ms[m] * 1e-3) for m in ms},
+            "cost_ratio_exact_over": {m: ms["exact"] / ms[m] for m in ("uv", "img")},
+            "uv_plane": res["uv"], "image_plane": res["img"],
+            "uv_better_than_img_at_every_radius": bool(np.all(
+                [res["uv"]["err_max_peak_normalised"][k] <= res["img"]["err_max_peak_normalised"][k]
+                 for k in res["uv"]["err_max_peak_normalised"]]))}
 
 
 def main():
@@ -248,7 +311,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c4"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures); c4: only the batched "
                          "256 x 64^2 measurement (profiler captures of the batched kernel)")
@@ -256,12 +319,19 @@ def main():
     rank, world, local = dist_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
-    if args.workload == "c4":
+    if args.workload in ("c3", "c4"):
         import torch
         import paper_2009_07010_gb300 as psf
         psf.build_library()
         torch.cuda.set_device(local)
-        print(json.dumps(measure_batched(psf, args.prec, steps=args.steps)), flush=True)
+        print(json.dumps(measure_batched(psf, args.prec, steps=args.steps, which=args.workload)), flush=True)
+        return 0
+    if args.workload == "c5":
+        import torch
+        import paper_2009_07010_gb300 as psf
+        psf.build_library()
+        torch.cuda.set_device(local)
+        print(json.dumps(measure_c5(psf, args.prec)), flush=True)
         return 0
 
     import torch
