@@ -36,6 +36,7 @@ constexpr int kInStages = 16;      // per-visibility input (uv, w) ring depth
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
 constexpr int kGenWarps = 16;      // two groups of 8, taking alternate stages
 constexpr int kGroupWarps = 8;
+constexpr int kGroups = kGenWarps / kGroupWarps;
 constexpr int kDrainWarp0 = 16;
 constexpr int kMmaWarp = 20;
 constexpr int kThreads = 21 * 32;
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int half = it.N / 2;
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
-        for (int s_i = grp; s_i < nst; s_i += 2) {
+        for (int s_i = grp; s_i < nst; s_i += kGroups) {
             const int slot = s_i % kStages;
             const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
             const int islot = s_i % kInStages;
