@@ -34,6 +34,7 @@ constexpr int kKrIn = 16;             // uv input ring depth (stages)
 constexpr int kKrKS = 32;             // visibilities per stage
 constexpr int kKrGenWarps = 16;       // two groups of 8 on alternate stages
 constexpr int kKrGroupWarps = 8;
+constexpr int kKrGroups = kKrGenWarps / kKrGroupWarps;
 constexpr int kKrFoldWarp0 = 16;
 constexpr int kKrTmaWarp = 20;
 constexpr int kKrMmaWarp = 21;
@@ -128,13 +129,9 @@ __global__ void __launch_bounds__(kKrThreads, 1)
         // ------------------------------------------------------------ pixel twiddles
         const int half = it.N / 2;
         const int grp = warp / kKrGroupWarps, gw = warp % kKrGroupWarps;
-        const int r0 = gw * 32;                           // this warp's 32 rows (pixels) of the B tile
-        const bool active = r0 < it.npx;
-        const int q = it.q0 + r0;
-        const int jrow = q / it.N, i0 = q - jrow * it.N;   // a 32-pixel run inside one cutout row
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
-        for (int s_i = grp; s_i < nst; s_i += 2) {
+        for (int s_i = grp; s_i < nst; s_i += kKrGroups) {
             const int slot = s_i % kKrStages;
             const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
             const int islot = s_i % kKrIn;
@@ -145,8 +142,10 @@ __global__ void __launch_bounds__(kKrThreads, 1)
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            if (active) {
-                const float tu = uvk.x * cell, tv = uvk.y * cell;
+            const float tu = uvk.x * cell, tv = uvk.y * cell;
+            for (int r0 = gw * 32; r0 < it.npx; r0 += kKrGroupWarps * 32) {   // 32-pixel runs of this warp
+                const int q = it.q0 + r0;
+                const int jrow = q / it.N, i0 = q - jrow * it.N;   // inside one cutout row
                 gen_run32<BF16>(smem_u32(b_base + slot * kKrBTile + r0 * 128), off8, tu, i0 - half,
                                 tv * (float)(jrow - half));
             }
