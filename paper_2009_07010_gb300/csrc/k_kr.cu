@@ -7,14 +7,15 @@
 // precomputed per position chunk into an FP16/BF16 buffer and loaded by 2-D TMA with
 // 128-byte swizzle), B'[q][2k] = Re KR, B'[q][2k+1] = Im KR (generated on chip).
 // One CTA computes a 128-position x 256-pixel tile over a range of visibilities:
-//   warps 0-7    generate the 256 pixel twiddles of each 32-visibility stage: each
+//   warps 0-15   (four groups on stages s mod 4) generate the 256 pixel twiddles of
+//                each 32-visibility stage: each
 //                lane owns one visibility and walks a 32-pixel run of one cutout row
 //                (phasor recurrence along l, seeded from the MUFU sine/cosine of the
 //                reduced phase u dl + v dm), FP16/BF16 pairs into the swizzled layout;
-//   warp 12      TMA producer of the weight tile of each stage;
-//   warp 13      TMEM allocation, the uv input ring (bulk copies) and the single-thread
+//   warp 20      TMA producer of the weight tile of each stage;
+//   warp 21      TMEM allocation, the uv input ring (bulk copies) and the single-thread
 //                tcgen05.mma issue (M = 128, N = 256, K = 16);
-//   warps 8-11   every kFoldStages stages add the active TMEM accumulator into a
+//   warps 16-19  every kFoldStages stages add the active TMEM accumulator into a
 //                running-sum region of TMEM (short FP32 accumulation runs); at the
 //                end they add sum + active into the output with global atomics (the
 //                output is zeroed first; several visibility ranges of a tile add up).
@@ -32,14 +33,17 @@ using namespace tc;
 constexpr int kKrStages = 4;
 constexpr int kKrIn = 16;             // uv input ring depth (stages)
 constexpr int kKrKS = 32;             // visibilities per stage
-constexpr int kKrGenWarps = 16;       // two groups of 8 on alternate stages
-constexpr int kKrGroupWarps = 8;
+constexpr int kKrGenWarps = 16;       // four groups of 4; group g generates stages s = g (mod 4)
+constexpr int kKrGroupWarps = 4;
 constexpr int kKrGroups = kKrGenWarps / kKrGroupWarps;
 constexpr int kKrFoldWarp0 = 16;
 constexpr int kKrTmaWarp = 20;
 constexpr int kKrMmaWarp = 21;
 constexpr int kKrThreads = 22 * 32;
 constexpr int kKrFoldStages = 64;
+// Slot-reuse parity waits stay unambiguous only with at most as many generator groups
+// as operand stages (see k_tc.cu).
+static_assert(kKrGroups <= kKrStages && kKrGroups <= kKrIn, "generator groups exceed a ring depth");
 constexpr uint32_t kKrATile = 128 * 128;   // 128 positions x 64 K' x 2 B
 constexpr uint32_t kKrBTile = 256 * 128;   // 256 pixels x 64 K' x 2 B
 constexpr uint32_t kKrInSlot = kKrKS * 8;  // uv per stage

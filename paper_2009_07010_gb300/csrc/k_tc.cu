@@ -7,14 +7,16 @@
 //   A'[j][2k] = Re c, A'[j][2k+1] = Im c,  B'[i][2k] = Re a, B'[i][2k+1] = -Im a,
 //   P = A' B'^T  with K' = 2K (FP16 or BF16 operands, FP32 accumulation in TMEM).
 //
-// Warp roles (416 threads):
-//   warps 0-7   operand generators: per pipeline stage of 32 visibilities each lane
+// Warp roles (672 threads):
+//   warps 0-15  operand generators (four groups on stages s mod 4, two chains per warp
+//               and stage): per pipeline stage of 32 visibilities each lane
 //               owns one visibility and walks a 32-row recurrence chain
 //               (seed and step from the MUFU sin/cos of the reduced phase, then
 //               complex multiplication), writing FP16/BF16 pairs straight into the
 //               128-byte-swizzled K-major shared-memory layout the MMA reads;
-//   warp 12     TMEM allocation and the single-thread tcgen05.mma issue loop;
-//   warps 8-11  drain: every kDrainStages stages the MMA switches to the second TMEM
+//   warp 20     TMEM allocation, the uv/w input ring (bulk copies) and the single-thread
+//               tcgen05.mma issue loop;
+//   warps 16-19 drain: every kDrainStages stages the MMA switches to the second TMEM
 //               accumulator while these warps read the first (tcgen05.ld) and add it
 //               into the CTA's FP32 partial tile in global memory.  Short TMEM
 //               accumulation runs bound the tensor-core rounding growth.
@@ -34,9 +36,15 @@ using namespace tc;
 
 constexpr int kInStages = 16;      // per-visibility input (uv, w) ring depth
 constexpr int kKS = 32;            // complex visibilities per stage (K' = 64 = one 128 B row)
-constexpr int kGenWarps = 16;      // two groups of 8, taking alternate stages
-constexpr int kGroupWarps = 8;
+constexpr int kGenWarps = 16;      // four groups of 4; group g generates stages s = g (mod 4)
+constexpr int kGroupWarps = 4;
 constexpr int kGroups = kGenWarps / kGroupWarps;
+// A group waiting for slot reuse (stage s - S consumed) must find the slot's previous
+// phase (stage s - 2S) already consumed, or the parity test of the barrier aliases;
+// that holds when the group's previous stage s - kGroups waited for stage
+// s - kGroups - S >= s - 2S, i.e. kGroups <= S for every ring depth S used (4, 6, 8).
+static_assert(kGroups <= 4, "generator groups must not exceed the smallest operand ring depth");
+static_assert(kGroups <= kInStages, "generator groups must not exceed the input ring depth");
 constexpr int kDrainWarp0 = 16;
 constexpr int kMmaWarp = 20;
 constexpr int kThreads = 21 * 32;
