@@ -67,11 +67,45 @@ __device__ __forceinline__ float ddirichlet(int F, float a) {
 
 __device__ __forceinline__ float dot3(float4 a, float4 L) { return a.x * L.x + a.y * L.y + a.z * L.z; }
 
+// Fast variants for weights that are rounded to FP16/BF16 afterwards (tensor-core
+// paths): the argument is reduced exactly to |r| <= 1/2 turn (x - rint(x)) and the
+// MUFU sine/cosine (__sinf, __sincosf, |error| ~ 1e-6 on [-pi, pi]) is used.
+__device__ __forceinline__ float sinpi_fast(float x) {   // sin(pi x)
+    const float n = rintf(x * 0.5f);
+    return __sinf(kPiF * (x - 2.0f * n));
+}
+__device__ __forceinline__ void sincospi2_fast(float x, float *s, float *c) {   // sin, cos of 2 pi x
+    const float r = x - rintf(x);
+    __sincosf(2.0f * kPiF * r, s, c);
+}
+__device__ __forceinline__ float sincpi_fast(float y) {
+    return y == 0.0f ? 1.0f : sinpi_fast(y) / (kPiF * y);
+}
+__device__ __forceinline__ float dirichlet_fast(int F, float a) {
+    if (F == 1) return 1.0f;
+    const float n = rintf(a);
+    const float r = a - n;
+    const float sgn = (((int)n * (F - 1)) & 1) ? -1.0f : 1.0f;
+    if (r == 0.0f) return sgn;
+    return sgn * sinpi_fast((float)F * r) / ((float)F * __sinf(kPiF * r));
+}
+
+// Uniform dispatch between the accurate and the fast forms.
+template <bool FAST>
+__device__ __forceinline__ float sincpi_t(float y) { return FAST ? sincpi_fast(y) : sincpi(y); }
+template <bool FAST>
+__device__ __forceinline__ float dirichlet_t(int F, float a) { return FAST ? dirichlet_fast(F, a) : dirichlet(F, a); }
+template <bool FAST>
+__device__ __forceinline__ void sincospi2_t(float x, float *s, float *c) {   // sin, cos of 2 pi x
+    if (FAST) sincospi2_fast(x, s, c);
+    else sincospif(2.0f * x, s, c);
+}
+
 // Exact bin average (Eq. 13), centre phase removed.  With uniform channels the
 // channel sum is the Dirichlet kernel times the per-channel sinc (exact identity
 // for equally spaced, equally wide channels); otherwise channels are summed.
 // grad (optional): d/dl0 (re, im), d/dm0 (re, im) with dL0/dl0 = dLl, dL0/dm0 = dLm.
-template <bool GRAD>
+template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, float4 L, float4 dLl,
                                                float4 dLm, float4 *grad) {
     const float4 ub = o.bin_ubar[bin];
@@ -87,14 +121,14 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
         const float Xs = Xbar + ds;
         // exp(-2 pi i nu_r ds / c): the sample's offset from the bin centre
         float sn, cs;
-        sincospif(-2.0f * ch.x * ds * kInvC, &sn, &cs);
+        sincospi2_t<FAST>(-ch.x * ds * kInvC, &sn, &cs);
         float dsl = 0.f, dsm = 0.f;
         if (GRAD) { dsl = dot3(d, dLl); dsm = dot3(d, dLm); }
         if (o.uniform) {
             const float a = ch.z * Xs * kInvC;
             const float y = ch.w * Xs * kInvC;
-            const float dir = dirichlet(o.favg, a);
-            const float sc = sincpi(y);
+            const float dir = dirichlet_t<FAST>(o.favg, a);
+            const float sc = sincpi_t<FAST>(y);
             const float f = dir * sc;
             re += cs * f;
             im += sn * f;
@@ -113,9 +147,9 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
             for (int c = 0; c < o.favg; ++c) {
                 const float4 rc = o.rawchan[r * o.favg + c];
                 float s2, c2;
-                sincospif(-2.0f * rc.x * Xs * kInvC, &s2, &c2);
+                sincospi2_t<FAST>(-rc.x * Xs * kInvC, &s2, &c2);
                 const float y = rc.y * Xs * kInvC;
-                const float S = sincpi(y) * rc.z;
+                const float S = sincpi_t<FAST>(y) * rc.z;
                 const float er = cs * c2 - sn * s2, ei = cs * s2 + sn * c2;
                 re += er * S;
                 im += ei * S;
@@ -138,7 +172,7 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
 }
 
 // Method 1 (Eqs. 31-35): sinc_pi(dedge.L0 nu_r / c) * sinc_pi(ubar.L0 Dnu_r / c).
-template <bool GRAD>
+template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, float4 L, float4 dLl,
                                             float4 dLm, float4 *grad) {
     const float4 ub = o.bin_ubar[bin];
@@ -146,7 +180,7 @@ __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, flo
     const float4 ch = o.chan[r];
     const float A = dot3(ed, L) * ch.x * kInvC;
     const float B = dot3(ub, L) * ch.y * kInvC;
-    const float sA = sincpi(A), sB = sincpi(B);
+    const float sA = sincpi_t<FAST>(A), sB = sincpi_t<FAST>(B);
     if (GRAD) {
         const float dA = dsincpi(A), dB = dsincpi(B);
         const float Al = dot3(ed, dLl) * ch.x * kInvC, Am = dot3(ed, dLm) * ch.x * kInvC;
@@ -160,7 +194,7 @@ __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, flo
 //   (du/dt, dv/dt) = omega_E (-v, u) for theta = atan2(v, u), or the literal
 //   arctan(u/v) reading when PSF_IMG_LITERAL_THETA is set;
 //   D = sinc_pi(omega_E Dt (udot l0 + vdot m0)) sinc_pi((Dnu/nu) |u| |l0|).
-template <bool GRAD>
+template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr_img(const DevObs &o, int bin, int r, float4 L,
                                              uint32_t flags, float4 *grad) {
     const float4 ub = o.bin_ubar[bin];
@@ -181,7 +215,7 @@ __device__ __forceinline__ float2 decorr_img(const DevObs &o, int bin, int r, fl
     const float fb = ch.y / ch.x * uvlen;
     const float A = wdt * (udot * L.x + vdot * L.y);
     const float B = fb * rho;
-    const float sA = sincpi(A), sB = sincpi(B);
+    const float sA = sincpi_t<FAST>(A), sB = sincpi_t<FAST>(B);
     if (GRAD) {
         const float dA = dsincpi(A), dB = dsincpi(B);
         const float Bl = rho > 0.f ? fb * L.x / rho : 0.f, Bm = rho > 0.f ? fb * L.y / rho : 0.f;
@@ -190,12 +224,12 @@ __device__ __forceinline__ float2 decorr_img(const DevObs &o, int bin, int r, fl
     return make_float2(sA * sB, 0.0f);
 }
 
-template <bool GRAD>
+template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr(const DevObs &o, int method, uint32_t flags, int bin, int r,
                                          float4 L, float4 dLl, float4 dLm, float4 *grad) {
-    if (method == kExact) return decorr_exact<GRAD>(o, bin, r, L, dLl, dLm, grad);
-    if (method == kUV) return decorr_uv<GRAD>(o, bin, r, L, dLl, dLm, grad);
-    return decorr_img<GRAD>(o, bin, r, L, flags, grad);
+    if (method == kExact) return decorr_exact<GRAD, FAST>(o, bin, r, L, dLl, dLm, grad);
+    if (method == kUV) return decorr_uv<GRAD, FAST>(o, bin, r, L, dLl, dLm, grad);
+    return decorr_img<GRAD, FAST>(o, bin, r, L, flags, grad);
 }
 
 }  // namespace psf

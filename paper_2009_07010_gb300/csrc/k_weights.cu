@@ -20,6 +20,7 @@
 namespace psf {
 
 // --------------------------------------------------------------- weights
+template <bool FAST>
 __global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t flags,
                                                  const float4 *__restrict__ pos, int32_t k0,
                                                  int32_t kn, float2 *__restrict__ w, int64_t ldw) {
@@ -31,23 +32,25 @@ __global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t 
     const int r = k - bin * o.nout;
     const float4 L = pos[p];
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 D = decorr<false>(o, method, flags, bin, r, L, z, z, nullptr);
+    float2 D = decorr<false, FAST>(o, method, flags, bin, r, L, z, z, nullptr);
     const float Wk = o.W[k];
     w[(int64_t)p * ldw + kk] = make_float2(Wk * D.x, Wk * D.y);
 }
 
 cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos, int npos,
-                           int32_t k0, int32_t kn, float2 *w, int64_t ldw, cudaStream_t st) {
+                           int32_t k0, int32_t kn, float2 *w, int64_t ldw, int fast, cudaStream_t st) {
     if (npos <= 0 || kn <= 0) return cudaSuccess;
     dim3 grid((kn + 255) / 256, npos);
-    k_weights<<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
+    if (fast) k_weights<true><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
+    else k_weights<false><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
     return cudaGetLastError();
 }
 
 // --------------------------------------------------------------- FP16/BF16 weights
 // Weights of a position chunk for the batched tensor-core contraction: row r holds
 // position slot_of_row[r] (zeros for padding rows, slot < 0) as (Re w, -Im w) pairs
-// at column pair (k - kc0); columns at or beyond kcn are zero.
+// at column pair (k - kc0); columns at or beyond kcn are zero.  The weights are
+// rounded to 16 bits, so the fast sine/cosine forms are used.
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_t flags,
                                                    const float4 *__restrict__ pos,
@@ -63,7 +66,7 @@ __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_
         const int bin = k / o.nout;
         const int r = k - bin * o.nout;
         const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float2 D = decorr<false>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
+        const float2 D = decorr<false, true>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
         const float Wk = o.W[k];
         w = make_float2(Wk * D.x, Wk * D.y);
     }

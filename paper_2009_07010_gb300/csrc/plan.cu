@@ -639,7 +639,7 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
         const int64_t ldw = (K + 31) / 32 * 32;
         PSF_TRY(p->wbuf.reserve((size_t)(cn * ldw + 64) * sizeof(float2)));
         float2 *w = (float2 *)p->wbuf.p;
-        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, st));
+        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, tc ? 1 : 0, st));
 
         p->n_kernels++;
         float *part = out;

@@ -44,8 +44,9 @@ enum Method { kExact = 0, kUV = 1, kImg = 2 };
 
 // ---- launchers (k_weights.cu) -------------------------------------------
 // w[s * ldw + (k - k0)] = W_k * D_k(pos[s]) for s < npos, k0 <= k < k0 + kn.
+// fast != 0: MUFU sine/cosine forms (for weights rounded to 16 bits afterwards).
 cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos,
-                           int npos, int32_t k0, int32_t kn, float2 *w, int64_t ldw,
+                           int npos, int32_t k0, int32_t kn, float2 *w, int64_t ldw, int fast,
                            cudaStream_t st);
 // FP32 CUDA-core contraction; partial[split * split_stride + out_off + j*N + i].
 cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles,
