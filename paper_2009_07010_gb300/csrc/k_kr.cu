@@ -46,7 +46,7 @@ constexpr int kKrFoldStages = 64;
 static_assert(kKrGroups <= kKrStages && kKrGroups <= kKrIn, "generator groups exceed a ring depth");
 constexpr uint32_t kKrATile = 128 * 128;   // 128 positions x 64 K' x 2 B
 constexpr uint32_t kKrBTile = 256 * 128;   // 256 pixels x 64 K' x 2 B
-constexpr uint32_t kKrInSlot = kKrKS * 8;  // uv per stage
+constexpr uint32_t kKrInSlot = 2 * kKrKS * 8;  // uv per stage (64 visibilities in the real form)
 constexpr uint32_t kKrSmemBytes =
     kKrStages * (kKrATile + kKrBTile) + kKrIn * kKrInSlot + 512 + 1024;
 
@@ -85,7 +85,41 @@ __device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8
     }
 }
 
+// Real-weight form: lane t owns visibilities 2t and 2t+1 of a 64-visibility stage and
+// stores the pair (Re KR_2t, Re KR_2t+1) per pixel; the recurrences are packed across
+// the two visibilities, four interleaved 8-pixel pieces.
 template <int BF16>
+__device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&off)[8], float2 ta, float2 tb,
+                                               int n0, float2 phi) {
+    // ta = (theta_u of visibility 2t, of 2t+1); phi likewise
+    float2 re[4], im[4];
+#pragma unroll
+    for (int pc = 0; pc < 4; ++pc) {
+        const float2 za = cis_turns(fmaf(ta.x, (float)(n0 + 8 * pc), phi.x));
+        const float2 zb = cis_turns(fmaf(ta.y, (float)(n0 + 8 * pc), phi.y));
+        re[pc] = make_float2(za.x, zb.x);
+        im[pc] = make_float2(za.y, zb.y);
+    }
+    const float2 sa = cis_turns(ta.x), sb = cis_turns(ta.y);
+    const float2 sr = make_float2(sa.x, sb.x), si = make_float2(sa.y, sb.y), nsi = make_float2(-sa.y, -sb.y);
+    (void)tb;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        // rows q, q+8, q+16, q+24 = pieces 0..3 at step q
+        stmatrix_x4(base + off[q], pack2<BF16>(re[0].x, re[0].y), pack2<BF16>(re[1].x, re[1].y),
+                    pack2<BF16>(re[2].x, re[2].y), pack2<BF16>(re[3].x, re[3].y));
+        if (q < 7) {
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const float2 t = __fmul2_rn(im[pp], nsi), u = __fmul2_rn(im[pp], sr);
+                im[pp] = __ffma2_rn(re[pp], si, u);
+                re[pp] = __ffma2_rn(re[pp], sr, t);
+            }
+        }
+    }
+}
+
+template <int BF16, int REAL>
 __global__ void __launch_bounds__(kKrThreads, 1)
     k_psf_kr(const __grid_constant__ CUtensorMap wmap, const KrItem *__restrict__ items, const float2 *__restrict__ uv,
              int32_t kchunk0, float cell, const int64_t *__restrict__ out_off, float *__restrict__ out, int *err) {
@@ -105,7 +139,8 @@ __global__ void __launch_bounds__(kKrThreads, 1)
 
     const KrItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nst = (it.ke - it.kb + kKrKS - 1) / kKrKS;
+    constexpr int KS = REAL ? 2 * kKrKS : kKrKS;   // visibilities per stage (64 K' either way)
+    const int nst = (it.ke - it.kb + KS - 1) / KS;
     const int nfold = (nst + kKrFoldStages - 1) / kKrFoldStages;
 
     if (threadIdx.x == 0) {
@@ -141,17 +176,30 @@ __global__ void __launch_bounds__(kKrThreads, 1)
             const int islot = s_i % kKrIn;
             bool ok = wait_bounded(&in_full[islot], (uint32_t)(s_i / kKrIn) & 1u, s_abort, err);
             if (!__all_sync(0xffffffffu, ok)) break;
-            const float2 uvk = reinterpret_cast<const float2 *>(in_base + islot * kKrInSlot)[lane];
+            const float2 *in_uv = reinterpret_cast<const float2 *>(in_base + islot * kKrInSlot);
+            float2 uva, uvb;
+            if (REAL) {
+                uva = in_uv[2 * lane];
+                uvb = in_uv[2 * lane + 1];
+            } else {
+                uva = in_uv[lane];
+                uvb = uva;
+            }
             if (s_i >= kKrStages) {
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            const float tu = uvk.x * cell, tv = uvk.y * cell;
             for (int r0 = gw * 32; r0 < it.npx; r0 += kKrGroupWarps * 32) {   // 32-pixel runs of this warp
                 const int q = it.q0 + r0;
                 const int jrow = q / it.N, i0 = q - jrow * it.N;   // inside one cutout row
-                gen_run32<BF16>(smem_u32(b_base + slot * kKrBTile + r0 * 128), off8, tu, i0 - half,
-                                tv * (float)(jrow - half));
+                const uint32_t dst = smem_u32(b_base + slot * kKrBTile + r0 * 128);
+                if (REAL)
+                    gen_run32_real<BF16>(dst, off8, make_float2(uva.x * cell, uvb.x * cell), make_float2(0.f, 0.f),
+                                         i0 - half,
+                                         make_float2(uva.y * cell * (float)(jrow - half),
+                                                     uvb.y * cell * (float)(jrow - half)));
+                else
+                    gen_run32<BF16>(dst, off8, uva.x * cell, i0 - half, uva.y * cell * (float)(jrow - half));
             }
             fence_proxy_async_smem();
             __syncwarp();
@@ -160,7 +208,7 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     } else if (warp == kKrTmaWarp) {
         // ------------------------------------------------------------ weight tiles
         if (lane == 0) {
-            const int x0 = 2 * (it.kb - kchunk0);
+            const int x0 = (REAL ? 1 : 2) * (it.kb - kchunk0);   // K' column of the item's first visibility
             for (int s_i = 0; s_i < nst; ++s_i) {
                 const int slot = s_i % kKrStages;
                 const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
@@ -176,8 +224,8 @@ __global__ void __launch_bounds__(kKrThreads, 1)
             const uint32_t idesc = idesc_f16(128, it.npx, BF16);
             auto load_uv = [&](int s) {
                 const int islot = s % kKrIn;
-                mbar_arrive_expect_tx(&in_full[islot], kKrInSlot);
-                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s * kKrKS, kKrInSlot, &in_full[islot]);
+                mbar_arrive_expect_tx(&in_full[islot], KS * 8);
+                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s * KS, KS * 8, &in_full[islot]);
             };
             for (int s = 0; s < kKrIn && s < nst; ++s) load_uv(s);
             const uint32_t a0 = smem_u32(a_base), b0 = smem_u32(b_base);
@@ -250,25 +298,31 @@ __global__ void __launch_bounds__(kKrThreads, 1)
 
 }  // namespace
 
-cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
-                          float cell, const int64_t *out_off, float *out, int bf16, int *err, cudaStream_t st) {
-    if (nitems <= 0) return cudaSuccess;
-    const CUtensorMap *m = (const CUtensorMap *)wmap;
-    cudaError_t e;
-    if (bf16) {
-        e = cudaFuncSetAttribute(k_psf_kr<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrSmemBytes);
-        if (e != cudaSuccess) return e;
-        k_psf_kr<1><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
-    } else {
-        e = cudaFuncSetAttribute(k_psf_kr<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKrSmemBytes);
-        if (e != cudaSuccess) return e;
-        k_psf_kr<0><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
-    }
+template <int BF16, int REAL>
+static cudaError_t launch_kr_t(const CUtensorMap *m, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
+                               float cell, const int64_t *out_off, float *out, int *err, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(k_psf_kr<BF16, REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kKrSmemBytes);
+    if (e != cudaSuccess) return e;
+    k_psf_kr<BF16, REAL><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
     return cudaGetLastError();
 }
 
-// 2-D tensor map over the FP16/BF16 weight buffer: dim0 = pitch (2 KC) elements,
-// dim1 = rows; box 64 x 128 elements (one 128-byte-swizzled stage of 128 positions).
+cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
+                          float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
+                          cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    const CUtensorMap *m = (const CUtensorMap *)wmap;
+    if (bf16)
+        return real ? launch_kr_t<1, 1>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st)
+                    : launch_kr_t<1, 0>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st);
+    return real ? launch_kr_t<0, 1>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st)
+                : launch_kr_t<0, 0>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st);
+}
+
+// 2-D tensor map over the FP16/BF16 weight buffer: dim0 = pitch elements (2 KC for
+// complex weights, KC for real ones), dim1 = rows; box 64 x 128 elements (one
+// 128-byte-swizzled stage of 128 positions).
 int make_weight_map(void *map_out, void *w16, int bf16, int64_t pitch_elems, int64_t rows) {
     typedef CUresult (*EncodeFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,

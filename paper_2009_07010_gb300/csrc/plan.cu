@@ -425,8 +425,13 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
     const int rows = ntile * 128;
     const int64_t K = p->nvis;
     const int bf16 = p->opts.prec == PSF_TC_BF16;
-    int64_t KC = (int64_t)(kW16Budget / ((size_t)rows * 4)) / 32 * 32;
-    KC = std::max<int64_t>(32, std::min<int64_t>(KC, (K + 31) / 32 * 32));
+    // Methods 1 and 2 have real weights: one K' column per visibility, 64-visibility
+    // stages; the exact method has complex weights: two columns, 32-visibility stages.
+    const int real = method != kExact;
+    const int64_t ks = real ? 64 : 32;
+    const size_t bytes_per = real ? 2 : 4;
+    int64_t KC = (int64_t)(kW16Budget / ((size_t)rows * bytes_per)) / 64 * 64;
+    KC = std::max<int64_t>(64, std::min<int64_t>(KC, (K + 63) / 64 * 64));
     const int64_t nchunk = (K + KC - 1) / KC;
     const int ptiles = N * N / 256;
     // positions, per-row slots, per-slot output offsets (uploaded once), items per chunk
@@ -438,14 +443,14 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
         slot_of_row[i] = i;
         outo[i] = h.out_off[idx[i]];
     }
-    PSF_TRY(p->w16.reserve((size_t)rows * KC * 4));
+    PSF_TRY(p->w16.reserve((size_t)rows * KC * bytes_per));
     CUtensorMapStub wmap;
-    int s = make_weight_map(&wmap, p->w16.p, bf16, 2 * KC, rows);
+    int s = make_weight_map(&wmap, p->w16.p, bf16, real ? KC : 2 * KC, rows);
     if (s) return s;
     const int64_t nbase = (int64_t)ntile * ptiles;
     for (int64_t c = 0; c < nchunk; ++c) {
         const int64_t kc0 = c * KC, kcn = std::min<int64_t>(KC, K - kc0);
-        const int64_t nst = (kcn + 31) / 32;
+        const int64_t nst = (kcn + ks - 1) / ks;
         // visibility splits: the number of CTAs (tiles x splits, one CTA per SM) should
         // fill whole waves; among split counts giving >= 2 waves (and >= 64 stages per
         // split) take the one with the best last-wave occupancy
@@ -475,8 +480,8 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
                     it.N = N;
                     it.q0 = q * 256;
                     it.npx = 256;
-                    it.kb = (int32_t)(kc0 + sp * sper * 32);
-                    it.ke = (int32_t)std::min<int64_t>(kc0 + kcn, kc0 + (sp + 1) * sper * 32);
+                    it.kb = (int32_t)(kc0 + sp * sper * ks);
+                    it.ke = (int32_t)std::min<int64_t>(kc0 + kcn, kc0 + (sp + 1) * sper * ks);
                     items.push_back(it);
                 }
         const size_t off_pos = 0;
@@ -515,7 +520,7 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
             PSF_TRY(cudaEventRecord(ev1, st));
         }
         PSF_TRY(launch_psf_kr(&wmap, (const KrItem *)(dm + off_items), (int)items.size(), p->d.uv, (int32_t)kc0,
-                              (float)h.cell, (const int64_t *)(dm + off_outo), out, bf16, (int *)p->err.p, st));
+                              (float)h.cell, (const int64_t *)(dm + off_outo), out, bf16, real, (int *)p->err.p, st));
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
         p->n_kernels++;

@@ -45,6 +45,8 @@ enum Method { kExact = 0, kUV = 1, kImg = 2 };
 // ---- launchers (k_weights.cu) -------------------------------------------
 // w[s * ldw + (k - k0)] = W_k * D_k(pos[s]) for s < npos, k0 <= k < k0 + kn.
 // fast != 0: MUFU sine/cosine forms (for weights rounded to 16 bits afterwards).
+// launch_weights16: complex methods write (Re w, -Im w) pairs, kpitch pairs per row;
+// real methods write one value per visibility, kpitch pairs = 2 kpitch visibilities.
 cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos,
                            int npos, int32_t k0, int32_t kn, float2 *w, int64_t ldw, int fast,
                            cudaStream_t st);
@@ -89,10 +91,12 @@ struct KrItem {
     int32_t N;        // cutout size (multiple of 32, <= 256)
     int32_t q0;       // first pixel (row-major) of the 256-pixel tile
     int32_t npx;      // pixels of the tile (256)
-    int32_t kb, ke;   // visibility range, kb - chunk start a multiple of 32
+    int32_t kb, ke;   // visibility range, kb - chunk start a multiple of the stage size (32 or 64)
 };
+// real != 0: real weights (Methods 1, 2), one K' column per visibility.
 cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
-                          float cell, const int64_t *out_off, float *out, int bf16, int *err, cudaStream_t st);
+                          float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
+                          cudaStream_t st);
 int make_weight_map(void *map_out, void *w16, int bf16, int64_t pitch_elems, int64_t rows);
 int kr_smem_bytes();
 cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const float4 *pos,
