@@ -198,25 +198,32 @@ def measure_batched(psf, prec, steps=2, which="c4"):
     peaks, src = load_peaks()
     plan = psf.Plan(obs, prec=prec)
     out = torch.empty(batch.total(), dtype=torch.float32, device="cuda")
-
-    def step():
-        for m in ("exact", "uv", "img"):
+    # per method: whole-call time and the contraction kernel's own time (CUDA events
+    # recorded by the library on the launching stream); algorithmic flops per term:
+    # 4 for the complex weights of the exact method, 2 for the real weights of the
+    # approximations (one multiply-add per pixel-visibility term)
+    per, total_ms = {}, 0.0
+    for m, fpt in (("exact", 4.0), ("uv", 2.0), ("img", 2.0)):
+        plan.forward(m, batch, out=out)
+        torch.cuda.synchronize()
+        plan.profile_read()
+        plan.profile_enable(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(steps):
             plan.forward(m, batch, out=out)
-    step()
-    torch.cuda.synchronize()
-    plan.profile_read()
-    plan.profile_enable(True)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        step()
-    e1.record()
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-    kms, nkc, nk = plan.profile_read()
-    plan.profile_enable(False)
-    per_launch_flops = 4.0 * K * bg.total_pixels() * steps * 3 / max(nkc, 1)
-    ach = per_launch_flops / (kms / max(nkc, 1) * 1e-3) / 1e12
+        e1.record()
+        torch.cuda.synchronize()
+        ms_m = e0.elapsed_time(e1) / steps
+        kms, nkc, _ = plan.profile_read()
+        plan.profile_enable(False)
+        tf = fpt * K * bg.total_pixels() * steps / (kms * 1e-3) / 1e12
+        per[m] = {"ms": ms_m, "terms_per_s": K * bg.total_pixels() / (ms_m * 1e-3),
+                  "kernel_ms": kms / steps, "kernel_launches_per_call": nkc / steps,
+                  "algorithmic_flops_per_term": fpt, "kernel_tflops": tf,
+                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"]}
+        total_ms += ms_m
+    ms = total_ms
     adj = None
     if which == "c4":   # adjoint of the exact method (FP32 CUDA cores)
         R = torch.randn(batch.total(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
@@ -236,9 +243,7 @@ def measure_batched(psf, prec, steps=2, which="c4"):
     name = "meerkat64_2h_8ch_bda_256pos_64px" if which == "c4" else "meerkat64_2h_8ch_bda_4096pos_32to256px"
     return {"workload": name, "nvis": K, "positions": bg.npos, "npix": sorted(set(int(x) for x in bg.npix)),
             "value": terms / (ms * 1e-3), "unit": "terms/s", "ms_per_step": ms, "methods": ["exact", "uv", "img"],
-            "kernel": "k_psf_kr (tcgen05 batched contraction)", "kernel_ms_per_launch": kms / max(nkc, 1),
-            "kernel_launches": nkc, "kernel_tflops": ach, "kernel_frac_of_peak": ach / peaks["bf16_tflops"],
-            "peak_source": src,
+            "kernel": "k_psf_kr (tcgen05 batched contraction)", "per_method": per, "peak_source": src,
             "adjoint_exact": adj}
 
 
