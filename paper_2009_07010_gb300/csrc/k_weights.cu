@@ -51,93 +51,111 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
 // position slot_of_row[r] (zeros for padding rows, slot < 0) as (Re w, -Im w) pairs
 // at column pair (k - kc0); columns at or beyond kcn are zero.  The weights are
 // rounded to 16 bits, so the fast sine/cosine forms are used.
+// One thread per visibility (column) and a block of kRowsPerBlock position rows: the
+// visibility's records (bin, channel, weight, raw samples) are loaded once and reused
+// for every row; each warp writes 32 consecutive columns of one row at a time.
+constexpr int kRowsPerBlock = 32;
+
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_t flags,
                                                    const float4 *__restrict__ pos,
-                                                   const int32_t *__restrict__ slot_of_row, int32_t kc0,
+                                                   const int32_t *__restrict__ slot_of_row, int rows, int32_t kc0,
                                                    int32_t kcn, int64_t kpitch, uint32_t *__restrict__ w16) {
-    const int row = blockIdx.y;
     const int32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
     if (kk >= kpitch) return;
-    const int slot = slot_of_row[row];
-    float2 w = make_float2(0.f, 0.f);
-    if (slot >= 0 && kk < kcn) {
-        const int32_t k = kc0 + kk;
-        const int bin = k / o.nout;
-        const int r = k - bin * o.nout;
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-        const float2 D = decorr<false, true>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
-        const float Wk = o.W[k];
-        w = make_float2(Wk * D.x, Wk * D.y);
+    const int row0 = blockIdx.y * kRowsPerBlock;
+    const bool valid = kk < kcn;
+    const int32_t k = kc0 + (valid ? kk : 0);
+    const int bin = k / o.nout;
+    const int r = k - bin * o.nout;
+    const float Wk = valid ? o.W[k] : 0.f;
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int row = row0; row < min(rows, row0 + kRowsPerBlock); ++row) {
+        const int slot = slot_of_row[row];
+        float2 w = make_float2(0.f, 0.f);
+        if (slot >= 0 && valid) {
+            const float2 D = decorr<false, true>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
+            w = make_float2(Wk * D.x, Wk * D.y);
+        }
+        uint32_t packed;
+        if (BF16) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(w.x, -w.y);
+            packed = *reinterpret_cast<uint32_t *>(&h);
+        } else {
+            __half2 h = __floats2half2_rn(w.x, -w.y);
+            packed = *reinterpret_cast<uint32_t *>(&h);
+        }
+        w16[(int64_t)row * kpitch + kk] = packed;
     }
-    uint32_t packed;
-    if (BF16) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(w.x, -w.y);
-        packed = *reinterpret_cast<uint32_t *>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(w.x, -w.y);
-        packed = *reinterpret_cast<uint32_t *>(&h);
-    }
-    w16[(int64_t)row * kpitch + kk] = packed;
 }
 
-// Real weights (Methods 1 and 2): one FP16/BF16 value W_k D_k per visibility; rows of
-// kpitch2 pairs = 2 kpitch2 visibilities.
+// Real weights (Methods 1 and 2): one FP16/BF16 value W_k D_k per visibility; a thread
+// owns the visibility pair (2 kp, 2 kp + 1) of a row (kpitch2 pairs per row).
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, uint32_t flags,
                                                         const float4 *__restrict__ pos,
-                                                        const int32_t *__restrict__ slot_of_row, int32_t kc0,
-                                                        int32_t kcn, int64_t kpitch2, uint32_t *__restrict__ w16) {
-    const int row = blockIdx.y;
-    const int32_t kp = blockIdx.x * blockDim.x + threadIdx.x;   // pair of visibilities 2 kp, 2 kp + 1
+                                                        const int32_t *__restrict__ slot_of_row, int rows,
+                                                        int32_t kc0, int32_t kcn, int64_t kpitch2,
+                                                        uint32_t *__restrict__ w16) {
+    const int32_t kp = blockIdx.x * blockDim.x + threadIdx.x;
     if (kp >= kpitch2) return;
-    const int slot = slot_of_row[row];
-    float w0 = 0.f, w1 = 0.f;
-    if (slot >= 0) {
-        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int row0 = blockIdx.y * kRowsPerBlock;
+    int bin[2], rr[2];
+    float Wk[2];
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            const int32_t kk = 2 * kp + e;
-            if (kk >= kcn) break;
-            const int32_t k = kc0 + kk;
-            const int bin = k / o.nout;
-            const int r = k - bin * o.nout;
-            const float2 D = decorr<false, true>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
-            const float wv = o.W[k] * D.x;
-            if (e == 0) w0 = wv; else w1 = wv;
+    for (int e = 0; e < 2; ++e) {
+        const int32_t kk = 2 * kp + e;
+        const bool valid = kk < kcn;
+        const int32_t k = kc0 + (valid ? kk : 0);
+        bin[e] = k / o.nout;
+        rr[e] = k - bin[e] * o.nout;
+        Wk[e] = valid ? o.W[k] : 0.f;
+    }
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int row = row0; row < min(rows, row0 + kRowsPerBlock); ++row) {
+        const int slot = slot_of_row[row];
+        float wv[2] = {0.f, 0.f};
+        if (slot >= 0) {
+            const float4 P = pos[slot];
+#pragma unroll
+            for (int e = 0; e < 2; ++e)
+                if (Wk[e] != 0.f) wv[e] = Wk[e] * decorr<false, true>(o, method, flags, bin[e], rr[e], P, z, z, nullptr).x;
         }
+        uint32_t packed;
+        if (BF16) {
+            __nv_bfloat162 h = __floats2bfloat162_rn(wv[0], wv[1]);
+            packed = *reinterpret_cast<uint32_t *>(&h);
+        } else {
+            __half2 h = __floats2half2_rn(wv[0], wv[1]);
+            packed = *reinterpret_cast<uint32_t *>(&h);
+        }
+        w16[(int64_t)row * kpitch2 + kp] = packed;
     }
-    uint32_t packed;
-    if (BF16) {
-        __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-        packed = *reinterpret_cast<uint32_t *>(&h);
-    } else {
-        __half2 h = __floats2half2_rn(w0, w1);
-        packed = *reinterpret_cast<uint32_t *>(&h);
-    }
-    w16[(int64_t)row * kpitch2 + kp] = packed;
 }
 
 cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const float4 *pos,
                              const int32_t *slot_of_row, int rows, int32_t kc0, int32_t kcn, int64_t kpitch,
                              int bf16, void *w16, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
+    const unsigned gy = (unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock);
     if (method != kExact) {   // real weights: kpitch pairs per row hold 2 kpitch visibilities
         const int64_t kp2 = kpitch / 2;
-        dim3 grid((unsigned)((kp2 + 255) / 256), rows);
+        dim3 grid((unsigned)((kp2 + 255) / 256), gy);
         if (bf16)
-            k_weights16_real<1><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kp2,
+            k_weights16_real<1><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, rows, kc0, kcn, kp2,
                                                       (uint32_t *)w16);
         else
-            k_weights16_real<0><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kp2,
+            k_weights16_real<0><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, rows, kc0, kcn, kp2,
                                                       (uint32_t *)w16);
         return cudaGetLastError();
     }
-    dim3 grid((unsigned)((kpitch + 255) / 256), rows);
+    dim3 grid((unsigned)((kpitch + 255) / 256), gy);
     if (bf16)
-        k_weights16<1><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kpitch, (uint32_t *)w16);
+        k_weights16<1><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, rows, kc0, kcn, kpitch,
+                                             (uint32_t *)w16);
     else
-        k_weights16<0><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, kc0, kcn, kpitch, (uint32_t *)w16);
+        k_weights16<0><<<grid, 256, 0, st>>>(o, method, flags, pos, slot_of_row, rows, kc0, kcn, kpitch,
+                                             (uint32_t *)w16);
     return cudaGetLastError();
 }
 
