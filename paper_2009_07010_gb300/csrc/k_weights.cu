@@ -133,10 +133,92 @@ __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, ui
     }
 }
 
+// Exact weights, eight output channels of one bin per thread (affine channels, the
+// group count nout a multiple of 8).  Per raw sample only the factor
+// exp(-2 pi i nu_r ds / c) depends on the channel r; with nu_r = nu_r0 + j dnu it is
+// e0 rho^j, e0 = exp(-2 pi i nu_r0 ds / c), rho = exp(-2 pi i dnu ds / c), so a sample
+// costs two phasors and a recurrence instead of eight.  The channel-independent factor
+// is the Dirichlet kernel of the raw channels times their sinc (Eq. 13, boxcar).
+template <int BF16>
+__global__ void __launch_bounds__(256) k_weights16_exact8(DevObs o, uint32_t flags, const float4 *__restrict__ pos,
+                                                          const int32_t *__restrict__ slot_of_row, int rows,
+                                                          int32_t kc0, int32_t kcn, int64_t kpitch,
+                                                          uint32_t *__restrict__ w16) {
+    const int32_t g = blockIdx.x * blockDim.x + threadIdx.x;   // group of 8 columns
+    if ((int64_t)g * 8 >= kpitch) return;
+    const int row0 = blockIdx.y * kRowsPerBlock;
+    const int32_t kk0 = 8 * g;
+    const bool valid = kk0 < kcn;   // kcn is a multiple of nout, hence of 8, unless the tail
+    const int32_t k0 = kc0 + (valid ? kk0 : 0);
+    const int bin = k0 / o.nout;
+    const int r0 = k0 - bin * o.nout;
+    const float4 ub = o.bin_ubar[bin];
+    const int2 sm = o.bin_samp[bin];
+    const float4 ch = o.chan[r0];
+    float Wk[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) Wk[j] = (valid && kk0 + j < kcn) ? o.W[k0 + j] : 0.f;
+    const float inv = 1.0f / (float)sm.y;
+    for (int row = row0; row < min(rows, row0 + kRowsPerBlock); ++row) {
+        const int slot = slot_of_row[row];
+        float re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
+        if (slot >= 0 && valid) {
+            const float4 L = pos[slot];
+            const float Xbar = dot3(ub, L);
+            for (int s = 0; s < sm.y; ++s) {
+                const float4 d = o.samp[sm.x + s];
+                const float ds = dot3(d, L);
+                const float Xs = Xbar + ds;
+                const float f = dirichlet_fast(o.favg, ch.z * Xs * kInvC) * sincpi_fast(ch.w * Xs * kInvC);
+                float es, ec, rs, rc;
+                sincospi2_fast(-ch.x * ds * kInvC, &es, &ec);
+                sincospi2_fast(-o.dnu_ch * ds * kInvC, &rs, &rc);
+                float er = ec * f, ei = es * f;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    re[j] += er;
+                    im[j] += ei;
+                    const float t = er * rc - ei * rs;
+                    ei = er * rs + ei * rc;
+                    er = t;
+                }
+            }
+        }
+        uint32_t packed[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float wr = Wk[j] * re[j] * inv, wi = Wk[j] * im[j] * inv;
+            if (BF16) {
+                __nv_bfloat162 h = __floats2bfloat162_rn(wr, -wi);
+                packed[j] = *reinterpret_cast<uint32_t *>(&h);
+            } else {
+                __half2 h = __floats2half2_rn(wr, -wi);
+                packed[j] = *reinterpret_cast<uint32_t *>(&h);
+            }
+        }
+        uint4 *dst = reinterpret_cast<uint4 *>(w16 + (int64_t)row * kpitch + kk0);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    }
+}
+
 cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const float4 *pos,
                              const int32_t *slot_of_row, int rows, int32_t kc0, int32_t kcn, int64_t kpitch,
                              int bf16, void *w16, cudaStream_t st) {
     if (rows <= 0) return cudaSuccess;
+    if (method == kExact && o.chan_affine && o.nout % 8 == 0 && kc0 % 8 == 0 && kpitch % 8 == 0) {
+        const unsigned gy = (unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock);
+        dim3 grid((unsigned)((kpitch / 8 + 255) / 256), gy);
+        if (bf16)
+            k_weights16_exact8<1><<<grid, 256, 0, st>>>(o, flags, pos, slot_of_row, rows, kc0, kcn, kpitch,
+                                                        (uint32_t *)w16);
+        else
+            k_weights16_exact8<0><<<grid, 256, 0, st>>>(o, flags, pos, slot_of_row, rows, kc0, kcn, kpitch,
+                                                        (uint32_t *)w16);
+        return cudaGetLastError();
+    }
     const unsigned gy = (unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock);
     if (method != kExact) {   // real weights: kpitch pairs per row hold 2 kpitch visibilities
         const int64_t kp2 = kpitch / 2;

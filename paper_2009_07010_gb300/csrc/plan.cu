@@ -291,7 +291,28 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->meta_done, cudaEventDisableTiming);
     if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_status(e)); }
 
+    // affine output channels (nu_r = nu_0 + r dnu, same spacing and width in every
+    // group): enables the per-bin channel recurrence of the exact weights
+    int affine = uniform && nout >= 2;
+    const double dnu_ch = nout >= 2 ? (h_chan[nout - 1].x - (double)h_chan[0].x) / (nout - 1) : 0.0;
+    if (affine) {
+        double nu0 = 0, nulast = 0;
+        for (int c = 0; c < o->favg; ++c) { nu0 += o->freq_hz[c]; nulast += o->freq_hz[(nout - 1) * o->favg + c]; }
+        nu0 /= o->favg;
+        nulast /= o->favg;
+        const double dd = (nulast - nu0) / (nout - 1);
+        for (int r = 0; r < nout && affine; ++r) {
+            double nur = 0;
+            for (int c = 0; c < o->favg; ++c) nur += o->freq_hz[r * o->favg + c];
+            nur /= o->favg;
+            if (std::fabs(nur - nu0 - r * dd) > 1e-9 * nur) affine = 0;
+            if (std::fabs(h_chan[r].z - h_chan[0].z) > 1e-6f * std::fabs(h_chan[0].z) + 1e-3f) affine = 0;
+            if (std::fabs(h_chan[r].w - h_chan[0].w) > 1e-6f * h_chan[0].w) affine = 0;
+        }
+    }
     DevObs &d = p->d;
+    d.chan_affine = affine;
+    d.dnu_ch = (float)dnu_ch;
     d.nvis = (int32_t)nvis; d.nbin = (int32_t)nbin; d.nout = nout; d.favg = o->favg; d.uniform = uniform;
     d.dt = (float)dt;
     d.bin_ubar = (const float4 *)p->bin_ubar.p;

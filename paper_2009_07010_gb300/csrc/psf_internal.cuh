@@ -21,6 +21,8 @@ struct DevObs {
     int32_t favg;          // raw channels per output channel
     int32_t uniform;       // 1: raw channels equally spaced with equal widths in every group
     float dt;              // raw sample spacing [s]
+    int32_t chan_affine;   // 1: nu_r = nu_0 + r dnu_ch exactly, equal spacing/width in every group
+    float dnu_ch;          // output channel spacing when chan_affine
     const float4 *bin_ubar;   // [nbin] bin-mean uvw [m] (x,y,z), Delta t_k [s] (w)
     const float4 *bin_edge;   // [nbin] uvw(t_e) - uvw(t_s) [m] (Eq. 33 edges)
     const int2 *bin_samp;     // [nbin] first raw-sample record, sample count

@@ -110,3 +110,19 @@ def test_batched_config4_subset(psf):
             e = _errors(got, ref, sel, batch, offs)
             assert e.max() <= 1e-4, (name, e.max())
         assert plan.sync_status() == 0
+
+
+def test_batched_exact_channel_recurrence_favg2(psf):
+    """Eight equally spaced output channels of two raw channels each: the exact
+    weights take the per-bin channel recurrence with the Dirichlet factor.  Few
+    visibilities (3 584), so the bound is a few FP16 unit roundoffs (2e-3)."""
+    obs = obsgen.tiny_obs(seed=11, nant=8, ntime=64, nchan=16, tavg=4, favg=2, dt=4.0, df=1.5e6,
+                          radius_m=4000.0)
+    batch = _mixed_batch(8, [(32, 34)], 0.04, 3e-5)
+    offs = obsgen.concat_pixels(batch)
+    sel = _sample(batch, offs, 4, 21)
+    with psf.Plan(obs, prec="tc_fp16") as plan:
+        got = plan.exact(psf.Batch.from_obsgen(batch)).cpu().numpy().astype(np.float64)
+        assert plan.sync_status() == 0
+    ref = oracle.psf(obs, oracle.EXACT, batch, pix_sel=sel)
+    assert _errors(got, ref, sel, batch, offs).max() <= 2e-3
