@@ -168,6 +168,25 @@ def run_reference(args, rank, world):
     return 0
 
 
+def parity_check(psf):
+    """Peak-normalised max error against the FP64 oracle on workload 1 (16 antennas,
+    172 800 visibilities, 64 x 64 at (0.02, 0.02)) for every precision and method."""
+    import oracle
+    obs = obsgen.config1_obs()
+    bg = obsgen.config1_batch()
+    batch = psf.Batch.from_obsgen(bg)
+    res = {}
+    refs = {m: oracle.psf(obs, mid, bg) for m, mid in (("exact", 0), ("uv", 1), ("img", 2))}
+    with psf.Plan(obs, prec="fp32") as plan:
+        for prec in ("fp32", "tc_fp16", "tc_bf16"):
+            plan.set_opts(prec=prec)
+            for m in ("exact", "uv", "img"):
+                got = plan.forward(m, batch).cpu().numpy().astype(np.float64)
+                res[f"{prec}/{m}"] = float(np.max(np.abs(got - refs[m])) / np.max(np.abs(refs[m])))
+    return {"workload": "16ant_1km_1h_4ch_64px", "metric": "max |P - P_oracle| / max |P_oracle|", "err_max": res,
+            "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3}}
+
+
 def cpu_baseline_sample(obs, batch):
     import oracle
     K = obs.nvis()
@@ -437,6 +456,7 @@ def main():
                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "ms_per_step": dt * 1e3}
 
     batched = None if args.no_batched else measure_batched(psf, args.prec)
+    parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
     if rank == 0:
         peaks, src = load_peaks()
@@ -460,6 +480,7 @@ def main():
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched,
+                "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)
     plan.close()
