@@ -13,14 +13,16 @@
 //                (phasor recurrence along l, seeded from the MUFU sine/cosine of the
 //                reduced phase u dl + v dm), FP16/BF16 pairs into the swizzled layout;
 //   warp 20      TMA producer of the weight tile of each stage;
-//   warp 21      TMEM allocation, the uv input ring (bulk copies) and the single-thread
-//                tcgen05.mma issue (M = 128, N = 256, K = 16);
+//   warp 21      TMEM allocation and the single-thread tcgen05.mma issue
+//                (M = 128, N = 256, K = 16);
+//   warp 22      the uv input ring (bulk copies), refilled when the generator group
+//                of a stage has read its slot;
 //   warps 16-19  every kFoldStages stages add the active TMEM accumulator into a
 //                running-sum region of TMEM (short FP32 accumulation runs); at the
 //                end they add sum + active into the output with global atomics (the
 //                output is zeroed first; several visibility ranges of a tile add up).
 // Every barrier wait is bounded (2 s); on expiry the CTA raises the error flag, stops,
-// waits for its issued MMAs and frees TMEM.
+// waits (bounded) for its copies in flight and issued MMAs and frees TMEM.
 #include "psf_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -39,7 +41,8 @@ constexpr int kKrGroups = kKrGenWarps / kKrGroupWarps;
 constexpr int kKrFoldWarp0 = 16;
 constexpr int kKrTmaWarp = 20;
 constexpr int kKrMmaWarp = 21;
-constexpr int kKrThreads = 22 * 32;
+constexpr int kKrInWarp = 22;
+constexpr int kKrThreads = 23 * 32;
 constexpr int kKrFoldStages = 64;
 // Slot-reuse parity waits stay unambiguous only with at most as many generator groups
 // as operand stages (see k_tc.cu).
@@ -131,11 +134,13 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     uint64_t *full = (uint64_t *)(in_base + kKrIn * kKrInSlot);
     uint64_t *empty = full + kKrStages;
     uint64_t *in_full = empty + kKrStages;
-    uint64_t *acc_full = in_full + kKrIn;
+    uint64_t *in_empty = in_full + kKrIn;
+    uint64_t *acc_full = in_empty + kKrIn;
     uint64_t *acc_empty = acc_full + 1;
     uint64_t *done_bar = acc_empty + 1;
     uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    volatile int no_abort = 0;   // teardown waits ignore the abort flag
 
     const KrItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -148,7 +153,10 @@ __global__ void __launch_bounds__(kKrThreads, 1)
             mbar_init(&full[s], kKrGroupWarps + 1);
             mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < kKrIn; ++s) mbar_init(&in_full[s], 1);
+        for (int s = 0; s < kKrIn; ++s) {
+            mbar_init(&in_full[s], 1);
+            mbar_init(&in_empty[s], kKrGroupWarps);
+        }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 4);
         mbar_init(done_bar, 1);
@@ -185,6 +193,8 @@ __global__ void __launch_bounds__(kKrThreads, 1)
                 uva = in_uv[lane];
                 uvb = uva;
             }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&in_empty[islot]);   // the input slot may be refilled
             if (s_i >= kKrStages) {
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
@@ -222,37 +232,54 @@ __global__ void __launch_bounds__(kKrThreads, 1)
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
             const uint32_t idesc = idesc_f16(128, it.npx, BF16);
-            auto load_uv = [&](int s) {
-                const int islot = s % kKrIn;
-                mbar_arrive_expect_tx(&in_full[islot], KS * 8);
-                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s * KS, KS * 8, &in_full[islot]);
-            };
-            for (int s = 0; s < kKrIn && s < nst; ++s) load_uv(s);
-            const uint32_t a0 = smem_u32(a_base), b0 = smem_u32(b_base);
-            int in_acc = 0, folds = 0;
+            // short per-stage issue path (the MMA issue blocks this thread): slot and
+            // phase by increment, descriptors by adding the slot offset to the address
+            // field, constant accumulate flags
+            const uint64_t ad0 = desc_sw128(smem_u32(a_base)), bd0 = desc_sw128(smem_u32(b_base));
+            int slot = 0, in_acc = 0, folds = 0;
+            uint32_t ph = 0;
             for (int s_i = 0; s_i < nst; ++s_i) {
-                const int slot = s_i % kKrStages;
-                const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
                 if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
-                if (s_i + kKrIn < nst) load_uv(s_i + kKrIn);
                 if (in_acc == 0 && folds > 0 && !wait_bounded(acc_empty, (uint32_t)(folds - 1) & 1u, s_abort, err))
                     break;
                 tc_fence_after();
-                const uint64_t ad = desc_sw128(a0 + slot * kKrATile);
-                const uint64_t bd = desc_sw128(b0 + slot * kKrBTile);
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    umma_f16(tmem, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
-                             (in_acc > 0 || kk > 0) ? 1u : 0u);
+                const uint64_t ad = ad0 + (uint64_t)(slot * (kKrATile >> 4));
+                const uint64_t bd = bd0 + (uint64_t)(slot * (kKrBTile >> 4));
+                if (in_acc == 0) umma_f16(tmem, ad, bd, idesc, 0u);
+                else umma_f16(tmem, ad, bd, idesc, 1u);
+                umma_f16(tmem, ad + 2, bd + 2, idesc, 1u);
+                umma_f16(tmem, ad + 4, bd + 4, idesc, 1u);
+                umma_f16(tmem, ad + 6, bd + 6, idesc, 1u);
                 umma_commit(&empty[slot]);
                 if (++in_acc == kKrFoldStages || s_i == nst - 1) {
                     umma_commit(acc_full);
                     ++folds;
                     in_acc = 0;
                 }
+                if (++slot == kKrStages) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
             }
             umma_commit(done_bar);
-            wait_bounded(done_bar, 0, s_abort, nullptr);
+            wait_bounded(done_bar, 0, &no_abort, err);   // even after an abort (time-limited)
+        }
+        __syncwarp();
+    } else if (warp == kKrInWarp) {
+        // ------------------------------------------------------------ uv input ring
+        if (lane == 0) {
+            int issued = 0;
+            for (int s_i = 0; s_i < nst; ++s_i) {
+                const int islot = s_i % kKrIn;
+                if (s_i >= kKrIn && !wait_bounded(&in_empty[islot], (uint32_t)(s_i / kKrIn - 1) & 1u, s_abort, err))
+                    break;
+                mbar_arrive_expect_tx(&in_full[islot], KS * 8);
+                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s_i * KS, KS * 8, &in_full[islot]);
+                issued = s_i + 1;
+            }
+            // every copy has landed before the CTA exits (the last use of each slot)
+            for (int s_i = max(0, issued - kKrIn); s_i < issued; ++s_i)
+                wait_bounded(&in_full[s_i % kKrIn], (uint32_t)(s_i / kKrIn) & 1u, &no_abort, err);
         }
         __syncwarp();
     } else {

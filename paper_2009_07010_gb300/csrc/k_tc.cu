@@ -7,23 +7,33 @@
 //   A'[j][2k] = Re c, A'[j][2k+1] = Im c,  B'[i][2k] = Re a, B'[i][2k+1] = -Im a,
 //   P = A' B'^T  with K' = 2K (FP16 or BF16 operands, FP32 accumulation in TMEM).
 //
-// Warp roles (672 threads):
+// Warp roles (736 threads):
 //   warps 0-15  operand generators (four groups on stages s mod 4, two chains per warp
 //               and stage): per pipeline stage of 32 visibilities each lane
 //               owns one visibility and walks a 32-row recurrence chain
 //               (seed and step from the MUFU sin/cos of the reduced phase, then
 //               complex multiplication), writing FP16/BF16 pairs straight into the
 //               128-byte-swizzled K-major shared-memory layout the MMA reads;
-//   warp 20     TMEM allocation, the uv/w input ring (bulk copies) and the single-thread
-//               tcgen05.mma issue loop;
-//   warps 16-19 drain: every kDrainStages stages the MMA switches to the second TMEM
-//               accumulator while these warps read the first (tcgen05.ld) and add it
-//               into the CTA's FP32 partial tile in global memory.  Short TMEM
-//               accumulation runs bound the tensor-core rounding growth.
-// Stages are handed over with mbarriers (generators -> MMA: `full`, MMA commit ->
+//   warps 20, 22  TMEM allocation and the tcgen05.mma issue: with NISS = 2 (tiles of at
+//               most 128 columns) warp 20 issues the even stages and warp 22 the odd
+//               ones, each into accumulators of its own, so that one issuer's barrier
+//               wait (an mbarrier round trip during which a lone issuer leaves the
+//               tensor core idle) overlaps the other issuer's MMAs; with NISS = 1
+//               warp 20 issues every stage;
+//   warp 21     the uv/w input ring: one bulk copy pair per stage, refilled when the
+//               generator group of the stage has read it (`in_empty`);
+//   warps 16-19 drain: every kDrainStages stages the issuers switch to their second
+//               TMEM accumulator while these warps read the first ones (tcgen05.ld),
+//               add them and add the sum into the CTA's FP32 partial tile in global
+//               memory.  Short TMEM accumulation runs bound the tensor-core rounding
+//               growth.
+// Stages are handed over with mbarriers (input copies -> generators: `in_full`,
+// generators -> input warp: `in_empty`, generators -> MMA: `full`, MMA commit ->
 // generators: `empty`, MMA commit -> drain: `acc_full`, drain -> MMA: `acc_empty`).
-// Every wait is bounded by a wall-clock limit; on expiry the CTA raises the plan's
-// error flag, stops all roles, waits (bounded) for its issued MMAs and frees TMEM.
+// An issuing thread does nothing per stage but wait, issue and commit: MMA issue
+// blocks the thread, so its serial latency bounds the stage rate.  Every wait is bounded by a wall-clock limit; on
+// expiry the CTA raises the plan's error flag, stops all roles, waits (bounded) for
+// its bulk copies and issued MMAs and frees TMEM.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -47,7 +57,9 @@ static_assert(kGroups <= 4, "generator groups must not exceed the smallest opera
 static_assert(kGroups <= kInStages, "generator groups must not exceed the input ring depth");
 constexpr int kDrainWarp0 = 16;
 constexpr int kMmaWarp = 20;
-constexpr int kThreads = 21 * 32;
+constexpr int kInWarp = 21;
+constexpr int kMma2Warp = 22;
+constexpr int kThreads = 23 * 32;
 constexpr int kDrainStages = 64;   // stages accumulated in TMEM between drains
 constexpr int kATileBytes = 128 * 128;
 // One 32-row twiddle chain of one visibility (this lane), rows r = 0..31 of `base`:
@@ -112,11 +124,11 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
     L.b_off = kStages * kATileBytes;
     L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
     L.bar_off = L.in_off + kInStages * kInSlotBytes;
-    L.bytes = L.bar_off + 512;   // 2 S + kInStages + 5 barriers (<= 37 x 8 B), TMEM address, abort flag
+    L.bytes = L.bar_off + 512;   // 2 S + 2 kInStages + 8 barriers (<= 56 x 8 B), TMEM address, abort flag
     return L;
 }
 
-template <int BF16, int kStages>
+template <int BF16, int kStages, int NISS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
              const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
@@ -128,11 +140,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
     uint64_t *empty = full + kStages;
     uint64_t *in_full = empty + kStages;
-    uint64_t *acc_full = in_full + kInStages;
-    uint64_t *acc_empty = acc_full + 2;
-    uint64_t *done_bar = acc_empty + 2;
-    uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
+    uint64_t *in_empty = in_full + kInStages;
+    uint64_t *acc_full = in_empty + kInStages;   // [issuer][buffer]
+    uint64_t *acc_empty = acc_full + 4;          // [buffer], shared by the issuers
+    uint64_t *done_bar = acc_empty + 2;          // [issuer]
+    uint32_t *s_tmem = (uint32_t *)(done_bar + 2);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
+    volatile int no_abort = 0;   // teardown waits ignore the abort flag
 
     const TcItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -146,17 +160,19 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(&full[s], kGroupWarps);
             mbar_init(&empty[s], 1);
         }
-        for (int s = 0; s < kInStages; ++s) mbar_init(&in_full[s], 1);
-        for (int a = 0; a < 2; ++a) {
-            mbar_init(&acc_full[a], 1);
-            mbar_init(&acc_empty[a], 4);
+        for (int s = 0; s < kInStages; ++s) {
+            mbar_init(&in_full[s], 1);
+            mbar_init(&in_empty[s], kGroupWarps);
         }
-        mbar_init(done_bar, 1);
+        for (int a = 0; a < 4; ++a) mbar_init(&acc_full[a], 1);
+        for (int a = 0; a < 2; ++a) mbar_init(&acc_empty[a], 4);
+        for (int a = 0; a < 2; ++a) mbar_init(&done_bar[a], 1);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // accumulator (issuer q, buffer b) at TMEM column (2 q + b) acc_cols
     if (warp == kMmaWarp) {
-        tmem_alloc(s_tmem, 2 * acc_cols);
+        tmem_alloc(s_tmem, 2 * NISS * acc_cols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -180,6 +196,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float2 *in_uv = (const float2 *)(smem + L.in_off + islot * kInSlotBytes);
             const float2 uvk = in_uv[lane];
             const float2 wk = (it.k0 + s_i * kKS + lane < it.k1) ? in_uv[kKS + lane] : make_float2(0.f, 0.f);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&in_empty[islot]);   // the input slot may be refilled
             if (s_i >= kStages) {
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
@@ -197,92 +215,138 @@ __global__ void __launch_bounds__(kThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(&full[slot]);
         }
-    } else if (warp == kMmaWarp) {
+    } else if (warp == kMmaWarp || (NISS == 2 && warp == kMma2Warp)) {
         // ------------------------------------------------------------ MMA issue
+        // Issuer q takes the stages s = q (mod NISS); with an even ring depth every
+        // slot belongs to one issuer.  Accumulation range d covers stages
+        // [d kDrainStages, (d + 1) kDrainStages) and uses buffer b = d mod 2.
         if (lane == 0) {
+            const int q = (warp == kMmaWarp) ? 0 : 1;
+            // The MMA issue blocks this thread until the tensor core takes the
+            // instruction, so the per-stage path is kept short: slot, phase and range
+            // by increment, descriptors by adding the slot offset to the 14-bit address
+            // field (shared addresses < 256 KB cannot carry out of it).
             const uint32_t idesc = idesc_f16(128, ncols, BF16);
-            int acc = 0, in_acc = 0;
-            int uses[2] = {0, 0};
-            const uint32_t a0 = smem_u32(smem + L.a_off), b0 = smem_u32(smem + L.b_off);
-            // input ring: stage s's uv and w (256 B each) into slot s % kInStages
+            const uint64_t ad0 = desc_sw128(smem_u32(smem + L.a_off));
+            const uint64_t bd0 = desc_sw128(smem_u32(smem + L.b_off));
+            int slot = q, r = q, d = 0;
+            uint32_t ph = 0;
+            for (int s_i = q; s_i < nst; s_i += NISS) {
+                if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
+                const int b = d & 1;
+                if (r == q && d >= 2 &&   // first own stage of a range: the buffer's last drain is done
+                    !wait_bounded(&acc_empty[b], (uint32_t)((d >> 1) - 1) & 1u, s_abort, err))
+                    break;
+                tc_fence_after();
+                const uint64_t ad = ad0 + (uint64_t)(slot * (kATileBytes >> 4));
+                const uint64_t bd = bd0 + (uint64_t)(slot * (bt_stride >> 4));
+                const uint32_t dt = tmem + (uint32_t)(2 * q + b) * acc_cols;
+                // K' = 16 per MMA = 32 bytes (descriptor units of 16 B: +2) of the 128-byte row
+                if (r == q) umma_f16(dt, ad, bd, idesc, 0u);
+                else umma_f16(dt, ad, bd, idesc, 1u);
+                umma_f16(dt, ad + 2, bd + 2, idesc, 1u);
+                umma_f16(dt, ad + 4, bd + 4, idesc, 1u);
+                umma_f16(dt, ad + 6, bd + 6, idesc, 1u);
+                umma_commit(&empty[slot]);
+                r += NISS;
+                if (r >= kDrainStages || s_i + NISS >= nst) umma_commit(&acc_full[2 * q + b]);
+                if (r >= kDrainStages) {
+                    r -= kDrainStages;
+                    ++d;
+                }
+                slot += NISS;
+                if (slot >= kStages) {
+                    slot -= kStages;
+                    ph ^= 1u;
+                }
+            }
+            // all issued MMAs complete before TMEM is released (waited for even after
+            // an abort; the wait is still time-limited)
+            umma_commit(&done_bar[q]);
+            wait_bounded(&done_bar[q], 0, &no_abort, err);
+        }
+        __syncwarp();
+    } else if (warp == kInWarp) {
+        // ------------------------------------------------------------ input ring
+        // stage s's uv and w (256 B each) into slot s % kInStages, once the generator
+        // group of stage s - kInStages has read that slot
+        if (lane == 0) {
             const float2 *wp = w + (int64_t)it.slot * ldw;
-            auto load_inputs = [&](int s) {
-                const int islot = s % kInStages;
+            int issued = 0;
+            for (int s_i = 0; s_i < nst; ++s_i) {
+                const int islot = s_i % kInStages;
+                if (s_i >= kInStages &&
+                    !wait_bounded(&in_empty[islot], (uint32_t)(s_i / kInStages - 1) & 1u, s_abort, err))
+                    break;
                 uint8_t *dst = smem + L.in_off + islot * kInSlotBytes;
-                const int32_t kb = it.k0 + s * kKS;
+                const int32_t kb = it.k0 + s_i * kKS;
                 mbar_arrive_expect_tx(&in_full[islot], kInSlotBytes);
                 bulk_g2s(dst, uv + kb, kKS * 8, &in_full[islot]);
                 bulk_g2s(dst + kKS * 8, wp + kb, kKS * 8, &in_full[islot]);
-            };
-            for (int s = 0; s < kInStages && s < nst; ++s) load_inputs(s);
-            for (int s_i = 0; s_i < nst; ++s_i) {
-                const int slot = s_i % kStages;
-                const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
-                if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
-                // the generators of stage s_i have read its inputs: refill the slot
-                if (s_i + kInStages < nst) load_inputs(s_i + kInStages);
-                if (in_acc == 0 && uses[acc] > 0 &&
-                    !wait_bounded(&acc_empty[acc], (uint32_t)(uses[acc] - 1) & 1u, s_abort, err))
-                    break;
-                tc_fence_after();
-                const uint64_t ad = desc_sw128(a0 + slot * kATileBytes);
-                const uint64_t bd = desc_sw128(b0 + slot * bt_stride);
-                const uint32_t dt = tmem + (uint32_t)acc * acc_cols;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)   // K' = 16 per MMA = 32 bytes of the 128-byte row
-                    umma_f16(dt, ad + (uint64_t)(2 * kk), bd + (uint64_t)(2 * kk), idesc,
-                             (in_acc > 0 || kk > 0) ? 1u : 0u);
-                umma_commit(&empty[slot]);
-                if (++in_acc == kDrainStages || s_i == nst - 1) {
-                    umma_commit(&acc_full[acc]);
-                    uses[acc]++;
-                    acc ^= 1;
-                    in_acc = 0;
-                }
+                issued = s_i + 1;
             }
-            // all issued MMAs complete before TMEM is released
-            umma_commit(done_bar);
-            wait_bounded(done_bar, 0, s_abort, nullptr);
+            // every copy has landed before the CTA exits (the last use of each slot)
+            for (int s_i = max(0, issued - kInStages); s_i < issued; ++s_i)
+                wait_bounded(&in_full[s_i % kInStages], (uint32_t)(s_i / kInStages) & 1u, &no_abort, err);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ drain
+        // The partial cutout is stored transposed (element (j, i) at i N + j), so the 32
+        // lanes of a warp (32 consecutive rows j, one column per access) touch one
+        // contiguous 128-byte line.
         const int q = warp - kDrainWarp0;          // TMEM lane quarter (warp % 4)
         const int j = it.j0 + q * 32 + lane;       // output row (m offset index)
-        float *dst = partial + (int64_t)it.split * split_stride + it.out_off + (int64_t)j * it.N + it.i0;
+        float *dst = partial + (int64_t)it.split * split_stride + it.out_off + (int64_t)it.i0 * it.N + j;
+        const int64_t cstride = it.N;
         const bool row_ok = j < it.N;
         const int ncol_valid = min(ncols, it.N - it.i0);
         if (nst == 0) {
             if (row_ok)
-                for (int c = 0; c < ncol_valid; ++c) dst[c] = 0.f;
+                for (int c = 0; c < ncol_valid; ++c) dst[c * cstride] = 0.f;
         }
         const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
         for (int d = 0; d < ndrain; ++d) {
-            const int acc = d & 1;
-            const bool ok = wait_bounded(&acc_full[acc], (uint32_t)(d >> 1) & 1u, s_abort, err);
+            const int b = d & 1;
+            // issuer 1 has a stage in range d unless the range holds a single stage
+            const bool two = (NISS == 2) && (min(nst, (d + 1) * kDrainStages) - d * kDrainStages > 1);
+            bool ok = wait_bounded(&acc_full[b], (uint32_t)(d >> 1) & 1u, s_abort, err);
+            if (two && ok) ok = wait_bounded(&acc_full[2 + b], (uint32_t)(d >> 1) & 1u, s_abort, err);
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
             tc_fence_after();
-            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)acc * acc_cols;
+            const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * acc_cols;
             for (int c0 = 0; c0 < ncols; c0 += 16) {
                 float v[16];
                 tmem_ld16(ta + (uint32_t)c0, v);
-                if (row_ok) {
+                if (two) {
+                    float v2[16];
+                    tmem_ld16(ta + 2u * acc_cols + (uint32_t)c0, v2);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int c = c0 + e;
-                        if (c < ncol_valid) dst[c] = (d == 0) ? v[e] : dst[c] + v[e];
+                    for (int e = 0; e < 16; ++e) v[e] += v2[e];
+                }
+                if (row_ok) {
+                    // eight loads in flight before their stores (one L2 round trip per eight)
+#pragma unroll
+                    for (int h = 0; h < 16; h += 8) {
+                        float o[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            o[e] = (d > 0 && c0 + h + e < ncol_valid) ? dst[(c0 + h + e) * cstride] : 0.f;
+#pragma unroll
+                        for (int e = 0; e < 8; ++e)
+                            if (c0 + h + e < ncol_valid) dst[(c0 + h + e) * cstride] = o[e] + v[h + e];
                     }
                 }
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_empty[acc]);
+            if (lane == 0) mbar_arrive(&acc_empty[b]);
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) tmem_dealloc(tmem, 2 * acc_cols);
+    if (warp == kMmaWarp) tmem_dealloc(tmem, 2 * NISS * acc_cols);
 }
 
 // Self-test: one 128 x n x 64 FP16 GEMM through the same layout, descriptors,
@@ -385,15 +449,16 @@ int selftest_timeout(int limit_ms) {
     return flag ? PSF_ETIMEOUT : PSF_OK;
 }
 
-template <int BF16, int S>
+template <int BF16, int S, int NISS>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                                int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
                                cudaStream_t st) {
     const SmemLayout L = smem_layout(ncols_max, S);
     const size_t bytes = L.bytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_psf_tc<BF16, S><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
+    k_psf_tc<BF16, S, NISS><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
                                                         err);
     return cudaGetLastError();
 }
@@ -403,8 +468,13 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
                           cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int S = stages_for(ncols_max);
-#define PSF_TC_CASE(B, SS) \
-    if (bf16 == B && S == SS) return launch_tc_t<B, SS>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err, st);
+    // two issuers while both double-buffered accumulator pairs fit in TMEM (<= 128 columns)
+#define PSF_TC_CASE(B, SS)                                                                                        \
+    if (bf16 == B && S == SS)                                                                                     \
+        return SS == 4 ? launch_tc_t<B, SS, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride,   \
+                                               err, st)                                                           \
+                       : launch_tc_t<B, SS, 2>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride,   \
+                                               err, st);
     PSF_TC_CASE(0, 4) PSF_TC_CASE(0, 6) PSF_TC_CASE(0, 8) PSF_TC_CASE(1, 4) PSF_TC_CASE(1, 6) PSF_TC_CASE(1, 8)
 #undef PSF_TC_CASE
     return cudaErrorInvalidValue;

@@ -366,24 +366,28 @@ cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const
 __global__ void __launch_bounds__(256) k_reduce(const float *__restrict__ partial, int nsplit,
                                                 int64_t stride, const int64_t *__restrict__ loc_offs,
                                                 const int64_t *__restrict__ out_offs,
-                                                const int32_t *__restrict__ npix, float *__restrict__ out) {
+                                                const int32_t *__restrict__ npix, int transposed,
+                                                float *__restrict__ out) {
     const int p = blockIdx.y;
-    const int64_t n2 = (int64_t)npix[p] * npix[p];
+    const int N = npix[p];
+    const int64_t n2 = (int64_t)N * N;
     const float *src = partial + loc_offs[p];
     float *dst = out + out_offs[p];
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n2; q += (int64_t)gridDim.x * blockDim.x) {
         double s = 0.0;
         for (int sp = 0; sp < nsplit; ++sp) s += (double)src[(int64_t)sp * stride + q];
-        dst[q] = (float)s;
+        // transposed partials hold (j, i) at q = i N + j
+        const int64_t o = transposed ? (q % N) * N + q / N : q;
+        dst[o] = (float)s;
     }
 }
 
 cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, const int64_t *loc_offs,
-                          const int64_t *out_offs, const int32_t *npix, int npos, float *out,
+                          const int64_t *out_offs, const int32_t *npix, int npos, int transposed, float *out,
                           cudaStream_t st) {
     if (npos <= 0) return cudaSuccess;
     dim3 grid(64, npos);
-    k_reduce<<<grid, 256, 0, st>>>(partial, nsplit, stride, loc_offs, out_offs, npix, out);
+    k_reduce<<<grid, 256, 0, st>>>(partial, nsplit, stride, loc_offs, out_offs, npix, transposed, out);
     return cudaGetLastError();
 }
 

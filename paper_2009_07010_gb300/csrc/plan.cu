@@ -699,7 +699,7 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
         p->n_contract++;
         p->n_kernels++;
         if (!direct) {
-            PSF_TRY(launch_reduce(part, nsplit, stride, d_loc, d_out, d_npix, cn, out, st));
+            PSF_TRY(launch_reduce(part, nsplit, stride, d_loc, d_out, d_npix, cn, tc ? 1 : 0, out, st));
             p->n_kernels++;
         }
     }

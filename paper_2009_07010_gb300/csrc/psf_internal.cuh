@@ -56,9 +56,10 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
 cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles,
                             int ntiles, int nsplit, int32_t kper, float cell, float *partial,
                             int64_t split_stride, cudaStream_t st);
-// out[out_off_p + q] = sum_s partial[s * stride + loc_off_p + q] (float64 sum).
+// out[out_off_p + q] = sum_s partial[s * stride + loc_off_p + q'] (float64 sum), where
+// q' = q for row-major partials and q' = i N + j for q = j N + i when `transposed`.
 cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, const int64_t *loc_offs,
-                          const int64_t *out_offs, const int32_t *npix, int npos, float *out,
+                          const int64_t *out_offs, const int32_t *npix, int npos, int transposed, float *out,
                           cudaStream_t st);
 // Plan-time per-visibility tables: uv[k] and, if natural, W[k] = tavg * favg.
 cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st);
@@ -79,6 +80,7 @@ struct TcItem {
     int32_t split;
     int64_t out_off;
 };
+// partial[split * split_stride + out_off + i*N + j] (transposed within each cutout).
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items,
                           int nitems, int ncols_max, int bf16, float cell, float *partial,
                           int64_t split_stride, int *err_flag, cudaStream_t st);
