@@ -57,11 +57,17 @@ constexpr uint32_t kKrSmemBytes =
 // r = 0..31, as eight interleaved 4-pixel pieces in packed FP32x2 recurrences.
 template <int BF16>
 __device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float phi) {
-    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3
-    float2 z[8];
-#pragma unroll
-    for (int pc = 0; pc < 8; ++pc) z[pc] = cis_turns(fmaf(theta, (float)(n0 + 4 * pc), phi));
+    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3; two
+    // sine/cosine evaluations (row 0, step), piece seeds by the 4- and 16-row strides
     const float2 st = cis_turns(theta);
+    float2 z[8];
+    z[0] = cis_turns(fmaf(theta, (float)n0, phi));
+    const float2 s2 = cmulf(st, st), s4 = cmulf(s2, s2), s8 = cmulf(s4, s4), s16 = cmulf(s8, s8);
+    z[1] = cmulf(z[0], s4);
+    z[2] = cmulf(z[0], s8);
+    z[3] = cmulf(z[1], s8);
+#pragma unroll
+    for (int pc = 4; pc < 8; ++pc) z[pc] = cmulf(z[pc - 4], s16);
 
     // packed pairs: P0 = rows (q, q+16), P1 = (q+8, q+24), P2 = (q+4, q+20), P3 = (q+12, q+28)
     float2 re[4], im[4];
@@ -95,15 +101,28 @@ template <int BF16>
 __device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&off)[8], float2 ta, float2 tb,
                                                int n0, float2 phi) {
     // ta = (theta_u of visibility 2t, of 2t+1); phi likewise
+    // piece seeds (rows 0, 8, 16, 24) from row 0 and the 8- and 16-row strides
+    // (squarings of the step): four sine/cosine evaluations per lane
+    const float2 sa = cis_turns(ta.x), sb = cis_turns(ta.y);
+    float2 za[4], zb[4];
+    za[0] = cis_turns(fmaf(ta.x, (float)n0, phi.x));
+    zb[0] = cis_turns(fmaf(ta.y, (float)n0, phi.y));
+    {
+        const float2 a2 = cmulf(sa, sa), a4 = cmulf(a2, a2), a8 = cmulf(a4, a4), a16 = cmulf(a8, a8);
+        const float2 b2 = cmulf(sb, sb), b4 = cmulf(b2, b2), b8 = cmulf(b4, b4), b16 = cmulf(b8, b8);
+        za[1] = cmulf(za[0], a8);
+        za[2] = cmulf(za[0], a16);
+        za[3] = cmulf(za[1], a16);
+        zb[1] = cmulf(zb[0], b8);
+        zb[2] = cmulf(zb[0], b16);
+        zb[3] = cmulf(zb[1], b16);
+    }
     float2 re[4], im[4];
 #pragma unroll
     for (int pc = 0; pc < 4; ++pc) {
-        const float2 za = cis_turns(fmaf(ta.x, (float)(n0 + 8 * pc), phi.x));
-        const float2 zb = cis_turns(fmaf(ta.y, (float)(n0 + 8 * pc), phi.y));
-        re[pc] = make_float2(za.x, zb.x);
-        im[pc] = make_float2(za.y, zb.y);
+        re[pc] = make_float2(za[pc].x, zb[pc].x);
+        im[pc] = make_float2(za[pc].y, zb[pc].y);
     }
-    const float2 sa = cis_turns(ta.x), sb = cis_turns(ta.y);
     const float2 sr = make_float2(sa.x, sb.x), si = make_float2(sa.y, sb.y), nsi = make_float2(-sa.y, -sb.y);
     (void)tb;
 #pragma unroll

@@ -68,18 +68,28 @@ constexpr int kATileBytes = 128 * 128;
 // (seeds at r = 0, 4, ..., 28) held in four packed FP32x2 pairs, so each step is four
 // independent packed complex multiplications, and the eight rows of a step leave in
 // two stmatrix.
-template <int BF16>
+// MIRROR: the chain also writes the complex conjugate of row r at row R0 - r (mbase =
+// tile + R0 * 128 with R0 a multiple of 8; the packed pair's imaginary half is the
+// high 16 bits, so conjugation is a sign-bit XOR), and with `tail` the conjugate of
+// the value one step past the last row at `tail_addr` (row 0 of the tile).
+template <int BF16, bool MIRROR = false>
 __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float2 wk,
-                                            bool weighted) {
-    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3
-    float2 z[8];
-#pragma unroll
-    for (int pc = 0; pc < 8; ++pc) z[pc] = cis_turns(theta * (float)(n0 + 4 * pc));
+                                            bool weighted, uint32_t mbase = 0, bool tail = false,
+                                            uint32_t tail_addr = 0) {
+    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3.  Two
+    // sine/cosine evaluations per chain (row 0 and the step); the piece seeds follow
+    // by complex multiplication with the 4- and 16-row strides (squarings of the
+    // step), which keeps the MUFU pipe to 4 instructions per 32 rows.
     const float2 st = cis_turns(theta);
-    if (weighted) {
+    float2 z[8];
+    z[0] = cis_turns(theta * (float)n0);
+    if (weighted) z[0] = cmulf(z[0], wk);
+    const float2 s2 = cmulf(st, st), s4 = cmulf(s2, s2), s8 = cmulf(s4, s4), s16 = cmulf(s8, s8);
+    z[1] = cmulf(z[0], s4);
+    z[2] = cmulf(z[0], s8);
+    z[3] = cmulf(z[1], s8);
 #pragma unroll
-        for (int pc = 0; pc < 8; ++pc) z[pc] = cmulf(z[pc], wk);
-    }
+    for (int pc = 4; pc < 8; ++pc) z[pc] = cmulf(z[pc - 4], s16);
     // packed pairs: P0 = rows (q, q+16), P1 = (q+8, q+24), P2 = (q+4, q+20), P3 = (q+12, q+28)
     float2 re[4], im[4];
     re[0] = make_float2(z[0].x, z[4].x); im[0] = make_float2(z[0].y, z[4].y);
@@ -90,10 +100,26 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         // rows q, q+8, q+16, q+24 and rows q+4, q+12, q+20, q+28
-        stmatrix_x4(base + off[q], pack2<BF16>(re[0].x, im[0].x), pack2<BF16>(re[1].x, im[1].x),
-                    pack2<BF16>(re[0].y, im[0].y), pack2<BF16>(re[1].y, im[1].y));
-        stmatrix_x4(base + off[q + 4], pack2<BF16>(re[2].x, im[2].x), pack2<BF16>(re[3].x, im[3].x),
-                    pack2<BF16>(re[2].y, im[2].y), pack2<BF16>(re[3].y, im[3].y));
+        // matrix m of a mirrored store at offset q' writes row R0 - (q' + 8 m), chunk
+        // (lane mod 8) swizzled with (-q') mod 8
+        constexpr uint32_t kConj = 0x80000000u;
+        const uint32_t ln = threadIdx.x & 31u, ca = ln & 7u;
+        {
+            const uint32_t v0 = pack2<BF16>(re[0].x, im[0].x), v1 = pack2<BF16>(re[1].x, im[1].x);
+            const uint32_t v2 = pack2<BF16>(re[0].y, im[0].y), v3 = pack2<BF16>(re[1].y, im[1].y);
+            stmatrix_x4(base + off[q], v0, v1, v2, v3);
+            if (MIRROR)
+                stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)q * 128u + ((ca ^ ((8u - q) & 7u)) << 4),
+                            v0 ^ kConj, v1 ^ kConj, v2 ^ kConj, v3 ^ kConj);
+        }
+        {
+            const uint32_t v4 = pack2<BF16>(re[2].x, im[2].x), v5 = pack2<BF16>(re[3].x, im[3].x);
+            const uint32_t v6 = pack2<BF16>(re[2].y, im[2].y), v7 = pack2<BF16>(re[3].y, im[3].y);
+            stmatrix_x4(base + off[q + 4], v4, v5, v6, v7);
+            if (MIRROR)
+                stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)(q + 4) * 128u + ((ca ^ ((4u - q) & 7u)) << 4),
+                            v4 ^ kConj, v5 ^ kConj, v6 ^ kConj, v7 ^ kConj);
+        }
         if (q < 3) {
 #pragma unroll
             for (int pp = 0; pp < 4; ++pp) {
@@ -102,6 +128,12 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
                 re[pp] = __ffma2_rn(re[pp], sr, t);
             }
         }
+    }
+    if (MIRROR && tail) {   // row 32 = piece 7 (row 31, the .y half of pair 3) one step on
+        const float r32 = re[3].y * st.x - im[3].y * st.y, i32 = re[3].y * st.y + im[3].y * st.x;
+        const uint32_t lane = threadIdx.x & 31u;
+        // row 0: chunk lane / 4 (unswizzled), pair lane mod 4
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + lane * 4u), "r"(pack2<BF16>(r32, -i32)) : "memory");
     }
 }
 
@@ -131,7 +163,7 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
 template <int BF16, int kStages, int NISS>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
-             const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
+             const TcItem *__restrict__ items, int ncols_max, float cell, int wreal, float *__restrict__ partial,
              int64_t split_stride, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the operand tiles (swizzle atoms)
@@ -183,8 +215,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (warp < kGenWarps) {
         // ------------------------------------------------------------ generators
         const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
-        const int nA = 4, nB = ncols / 32;   // 32-row chains of the A (128 rows) and B tiles
         const int half = it.N / 2;
+        // Conjugate symmetry about the cutout centre (pixel offsets (r - N/2) cell):
+        // row N - r of the row twiddles holds the conjugate of row r, and so do the
+        // column twiddles when the weights are real (uv and image-plane methods).  For
+        // a tile that spans a whole cutout of 64 or 128 pixels only rows N/2 .. N-1 are
+        // generated; rows 1 .. N/2 are their conjugates and row 0 the conjugate of the
+        // value one step past row N-1.
+        const bool mirror = wreal && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0;
+        const int nA = mirror ? it.N / 64 : 4;            // 32-row chains of the A (128 rows) and B tiles
+        const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
         for (int s_i = grp; s_i < nst; s_i += kGroups) {
@@ -205,11 +245,20 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kATileBytes);
             const uint32_t b_tile = smem_u32(smem + L.b_off + slot * bt_stride);
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
-                if (ch < nA)   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
+                if (mirror) {   // rows R0 .. R0+31 (R0 = N/2 + 32 c) and their mirrors N - R0 - r
+                    const bool isA = ch < nA;
+                    const int c = isA ? ch : ch - nA;
+                    const int R0 = half + 32 * c;
+                    const uint32_t tile = isA ? a_tile : b_tile;
+                    gen_chain32<BF16, true>(tile + (uint32_t)R0 * 128u, off8, isA ? uvk.y * cell : -uvk.x * cell,
+                                            32 * c, wk, isA, tile + (uint32_t)(it.N - R0) * 128u, c == nA - 1,
+                                            tile);
+                } else if (ch < nA) {   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
                     gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk, true);
-                else           // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
+                } else {                // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
                     gen_chain32<BF16>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
                                       it.i0 + (ch - nA) * 32 - half, wk, false);
+                }
             }
             fence_proxy_async_smem();
             __syncwarp();
@@ -451,30 +500,30 @@ int selftest_timeout(int limit_ms) {
 
 template <int BF16, int S, int NISS>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
-                               int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
-                               cudaStream_t st) {
+                               int ncols_max, float cell, int wreal, float *partial, int64_t split_stride,
+                               int *err, cudaStream_t st) {
     const SmemLayout L = smem_layout(ncols_max, S);
     const size_t bytes = L.bytes + 1024;
     cudaError_t e =
         cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_psf_tc<BF16, S, NISS><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial, split_stride,
-                                                        err);
+    k_psf_tc<BF16, S, NISS><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, wreal, partial,
+                                                              split_stride, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
-                          int ncols_max, int bf16, float cell, float *partial, int64_t split_stride, int *err,
-                          cudaStream_t st) {
+                          int ncols_max, int bf16, float cell, int wreal, float *partial, int64_t split_stride,
+                          int *err, cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
     const int S = stages_for(ncols_max);
     // two issuers while both double-buffered accumulator pairs fit in TMEM (<= 128 columns)
 #define PSF_TC_CASE(B, SS)                                                                                        \
     if (bf16 == B && S == SS)                                                                                     \
-        return SS == 4 ? launch_tc_t<B, SS, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride,   \
-                                               err, st)                                                           \
-                       : launch_tc_t<B, SS, 2>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride,   \
-                                               err, st);
+        return SS == 4 ? launch_tc_t<B, SS, 1>(o, w, ldw, items, nitems, ncols_max, cell, wreal, partial,          \
+                                               split_stride, err, st)                                                           \
+                       : launch_tc_t<B, SS, 2>(o, w, ldw, items, nitems, ncols_max, cell, wreal, partial,          \
+                                               split_stride, err, st);
     PSF_TC_CASE(0, 4) PSF_TC_CASE(0, 6) PSF_TC_CASE(0, 8) PSF_TC_CASE(1, 4) PSF_TC_CASE(1, 6) PSF_TC_CASE(1, 8)
 #undef PSF_TC_CASE
     return cudaErrorInvalidValue;

@@ -693,7 +693,8 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
                                     kper, (float)h.cell, part, stride, st));
         } else {
             PSF_TRY(launch_psf_tc(p->d, w, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
-                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, part, stride, (int *)p->err.p, st));
+                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, method != PSF_METHOD_EXACT ? 1 : 0,
+                                  part, stride, (int *)p->err.p, st));
         }
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
