@@ -160,10 +160,13 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
     return L;
 }
 
-template <int BF16, int kStages, int NISS>
+// MIR: the weights of the launch are real, so whole-cutout tiles may use the
+// conjugate-symmetric generation (a separate instance keeps its register pressure out
+// of the complex-weight kernel).
+template <int BF16, int kStages, int NISS, int MIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
-             const TcItem *__restrict__ items, int ncols_max, float cell, int wreal, float *__restrict__ partial,
+             const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
              int64_t split_stride, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the operand tiles (swizzle atoms)
@@ -222,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // a tile that spans a whole cutout of 64 or 128 pixels only rows N/2 .. N-1 are
         // generated; rows 1 .. N/2 are their conjugates and row 0 the conjugate of the
         // value one step past row N-1.
-        const bool mirror = wreal && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0;
+        const bool mirror = MIR && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0;
         const int nA = mirror ? it.N / 64 : 4;            // 32-row chains of the A (128 rows) and B tiles
         const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
@@ -498,17 +501,17 @@ int selftest_timeout(int limit_ms) {
     return flag ? PSF_ETIMEOUT : PSF_OK;
 }
 
-template <int BF16, int S, int NISS>
+template <int BF16, int S, int NISS, int MIR>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
-                               int ncols_max, float cell, int wreal, float *partial, int64_t split_stride,
-                               int *err, cudaStream_t st) {
+                               int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
+                               cudaStream_t st) {
     const SmemLayout L = smem_layout(ncols_max, S);
     const size_t bytes = L.bytes + 1024;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bytes);
     if (e != cudaSuccess) return e;
-    k_psf_tc<BF16, S, NISS><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, wreal, partial,
-                                                              split_stride, err);
+    k_psf_tc<BF16, S, NISS, MIR><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial,
+                                                                   split_stride, err);
     return cudaGetLastError();
 }
 
@@ -518,12 +521,14 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
     if (nitems <= 0) return cudaSuccess;
     const int S = stages_for(ncols_max);
     // two issuers while both double-buffered accumulator pairs fit in TMEM (<= 128 columns)
-#define PSF_TC_CASE(B, SS)                                                                                        \
-    if (bf16 == B && S == SS)                                                                                     \
-        return SS == 4 ? launch_tc_t<B, SS, 1>(o, w, ldw, items, nitems, ncols_max, cell, wreal, partial,          \
-                                               split_stride, err, st)                                                           \
-                       : launch_tc_t<B, SS, 2>(o, w, ldw, items, nitems, ncols_max, cell, wreal, partial,          \
-                                               split_stride, err, st);
+#define PSF_TC_CASE(B, SS)                                                                                  \
+    if (bf16 == B && S == SS) {                                                                             \
+        constexpr int NI = SS == 4 ? 1 : 2;                                                                 \
+        return wreal ? launch_tc_t<B, SS, NI, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial,         \
+                                                 split_stride, err, st)                                      \
+                     : launch_tc_t<B, SS, NI, 0>(o, w, ldw, items, nitems, ncols_max, cell, partial,         \
+                                                 split_stride, err, st);                                     \
+    }
     PSF_TC_CASE(0, 4) PSF_TC_CASE(0, 6) PSF_TC_CASE(0, 8) PSF_TC_CASE(1, 4) PSF_TC_CASE(1, 6) PSF_TC_CASE(1, 8)
 #undef PSF_TC_CASE
     return cudaErrorInvalidValue;
