@@ -107,7 +107,12 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
         {
             const uint32_t v0 = pack2<BF16>(re[0].x, im[0].x), v1 = pack2<BF16>(re[1].x, im[1].x);
             const uint32_t v2 = pack2<BF16>(re[0].y, im[0].y), v3 = pack2<BF16>(re[1].y, im[1].y);
-            stmatrix_x4(base + off[q], v0, v1, v2, v3);
+            // without mirroring the row addresses are recomputed from the lane (cheaper than
+            // holding eight offsets at this kernel's register budget)
+            stmatrix_x4(MIRROR ? base + off[q]
+                               : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)q * 128u +
+                                     (((threadIdx.x & 7u) ^ (uint32_t)q) << 4),
+                        v0, v1, v2, v3);
             if (MIRROR)
                 stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)q * 128u + ((ca ^ ((8u - q) & 7u)) << 4),
                             v0 ^ kConj, v1 ^ kConj, v2 ^ kConj, v3 ^ kConj);
@@ -115,7 +120,10 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
         {
             const uint32_t v4 = pack2<BF16>(re[2].x, im[2].x), v5 = pack2<BF16>(re[3].x, im[3].x);
             const uint32_t v6 = pack2<BF16>(re[2].y, im[2].y), v7 = pack2<BF16>(re[3].y, im[3].y);
-            stmatrix_x4(base + off[q + 4], v4, v5, v6, v7);
+            stmatrix_x4(MIRROR ? base + off[q + 4]
+                               : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)(q + 4) * 128u +
+                                     (((threadIdx.x & 7u) ^ (uint32_t)(q + 4)) << 4),
+                        v4, v5, v6, v7);
             if (MIRROR)
                 stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)(q + 4) * 128u + ((ca ^ ((4u - q) & 7u)) << 4),
                             v4 ^ kConj, v5 ^ kConj, v6 ^ kConj, v7 ^ kConj);
