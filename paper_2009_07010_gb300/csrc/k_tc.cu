@@ -168,9 +168,10 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
     return L;
 }
 
-// MIR: the weights of the launch are real, so whole-cutout tiles may use the
+// MIR: 1 = the weights of the launch are real, so whole-cutout tiles may use the
 // conjugate-symmetric generation (a separate instance keeps its register pressure out
-// of the complex-weight kernel).
+// of the complex-weight kernel); 2 = real weights and every tile of the launch spans
+// a whole 64- or 128-pixel cutout (no unmirrored path compiled in).
 template <int BF16, int kStages, int NISS, int MIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
@@ -233,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // a tile that spans a whole cutout of 64 or 128 pixels only rows N/2 .. N-1 are
         // generated; rows 1 .. N/2 are their conjugates and row 0 the conjugate of the
         // value one step past row N-1.
-        const bool mirror = MIR && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0;
+        const bool mirror = (MIR == 2) || (MIR == 1 && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0);
         const int nA = mirror ? it.N / 64 : 4;            // 32-row chains of the A (128 rows) and B tiles
         const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
@@ -532,6 +533,9 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
 #define PSF_TC_CASE(B, SS)                                                                                  \
     if (bf16 == B && S == SS) {                                                                             \
         constexpr int NI = SS == 4 ? 1 : 2;                                                                 \
+        if (wreal == 2)                                                                                     \
+            return launch_tc_t<B, SS, NI, 2>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, \
+                                             err, st);                                                      \
         return wreal ? launch_tc_t<B, SS, NI, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial,         \
                                                  split_stride, err, st)                                      \
                      : launch_tc_t<B, SS, NI, 0>(o, w, ldw, items, nitems, ncols_max, cell, partial,         \

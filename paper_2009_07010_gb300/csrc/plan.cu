@@ -692,9 +692,15 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
             PSF_TRY(launch_psf_fp32(p->d, w, ldw, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
                                     kper, (float)h.cell, part, stride, st));
         } else {
+            int wreal = method != PSF_METHOD_EXACT ? 1 : 0;
+            if (wreal) {
+                bool whole = true;
+                for (const auto &t : items)
+                    whole = whole && t.j0 == 0 && t.i0 == 0 && t.ncols == t.N && t.N <= 128 && (t.N % 64) == 0;
+                if (whole) wreal = 2;
+            }
             PSF_TRY(launch_psf_tc(p->d, w, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
-                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, method != PSF_METHOD_EXACT ? 1 : 0,
-                                  part, stride, (int *)p->err.p, st));
+                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, wreal, part, stride, (int *)p->err.p, st));
         }
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;

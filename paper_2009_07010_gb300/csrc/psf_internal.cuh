@@ -81,8 +81,10 @@ struct TcItem {
     int64_t out_off;
 };
 // partial[split * split_stride + out_off + i*N + j] (transposed within each cutout).
-// wreal: the weights of this launch are real (imaginary parts zero), which allows the
-// conjugate-symmetric generation of the column twiddles.
+// wreal: 0 = complex weights; 1 = the weights of this launch are real (imaginary parts
+// zero), which allows the conjugate-symmetric generation of the column twiddles; 2 =
+// real weights and every item spans a whole cutout of 64 or 128 pixels (i0 = j0 = 0,
+// ncols = N), so every tile is generated conjugate-symmetrically.
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items,
                           int nitems, int ncols_max, int bf16, float cell, int wreal, float *partial,
                           int64_t split_stride, int *err_flag, cudaStream_t st);
