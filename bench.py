@@ -38,7 +38,7 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # DRAM bytes (read + write) per contraction launch from the ncu capture summarised in
 # profiles/k_psf_tc_meerkat64_1h_128px.md, per visibility (traffic is proportional to
 # K), valid only for the kernel source it was taken on.
-PROFILED_TRAFFIC = {"kernel_sha256_prefix": "dcb11256df1b57dd", "bytes_per_vis": (232.288000e6 + 3.296000e6) / 14515200,
+PROFILED_TRAFFIC = {"kernel_sha256_prefix": "4ecdc63840e7f1e8", "bytes_per_vis": (232.441088e6 + 3.470848e6) / 14515200,
                     "profile": "profiles/k_psf_tc_meerkat64_1h_128px.md"}
 
 

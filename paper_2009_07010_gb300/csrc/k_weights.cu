@@ -15,6 +15,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
+
 #include "decorr.cuh"
 
 namespace psf {
@@ -24,23 +26,31 @@ template <bool FAST>
 __global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t flags,
                                                  const float4 *__restrict__ pos, int32_t k0,
                                                  int32_t kn, float2 *__restrict__ w, int64_t ldw) {
+    // grid-stride over the visibilities (a few waves of blocks rather than one thread
+    // per visibility: the per-visibility work is a handful of loads and sines)
     const int p = blockIdx.y;
-    const int32_t kk = blockIdx.x * blockDim.x + threadIdx.x;
-    if (kk >= kn) return;
-    const int32_t k = k0 + kk;
-    const int bin = k / o.nout;
-    const int r = k - bin * o.nout;
     const float4 L = pos[p];
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    float2 D = decorr<false, FAST>(o, method, flags, bin, r, L, z, z, nullptr);
-    const float Wk = o.W[k];
-    w[(int64_t)p * ldw + kk] = make_float2(Wk * D.x, Wk * D.y);
+    for (int32_t kk = blockIdx.x * blockDim.x + threadIdx.x; kk < kn; kk += gridDim.x * blockDim.x) {
+        const int32_t k = k0 + kk;
+        const int bin = k / o.nout;
+        const int r = k - bin * o.nout;
+        float2 D = decorr<false, FAST>(o, method, flags, bin, r, L, z, z, nullptr);
+        const float Wk = o.W[k];
+        w[(int64_t)p * ldw + kk] = make_float2(Wk * D.x, Wk * D.y);
+    }
 }
 
 cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos, int npos,
                            int32_t k0, int32_t kn, float2 *w, int64_t ldw, int fast, cudaStream_t st) {
     if (npos <= 0 || kn <= 0) return cudaSuccess;
-    dim3 grid((kn + 255) / 256, npos);
+    static int nsm = 0;   // SM count of the first device used (only sizes the grid)
+    if (nsm == 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) {
+        cudaGetLastError();
+        nsm = 152;
+    }
+    const int64_t blocks = std::min<int64_t>((kn + 255) / 256, (int64_t)nsm * 16 / std::max(1, std::min(npos, 16)));
+    dim3 grid((unsigned)std::max<int64_t>(1, blocks), npos);
     if (fast) k_weights<true><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
     else k_weights<false><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
     return cudaGetLastError();
