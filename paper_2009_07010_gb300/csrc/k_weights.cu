@@ -41,6 +41,54 @@ __global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t 
     }
 }
 
+// Exact-method weights of the tensor-core paths (FP32 (Re w, Im w) per position row,
+// MUFU sine/cosine after exact argument reduction) by the per-bin channel recurrence
+// of k_weights16_exact8: a thread owns eight consecutive channels of one bin, and per
+// raw sample two phasors and a complex recurrence replace eight phasors.
+__global__ void __launch_bounds__(256) k_weights_exact8(DevObs o, const float4 *__restrict__ pos, int32_t k0,
+                                                        int32_t kn, float2 *__restrict__ w, int64_t ldw) {
+    const int p = blockIdx.y;
+    const float4 L = pos[p];
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; (int64_t)g * 8 < kn; g += gridDim.x * blockDim.x) {
+        const int32_t kk0 = 8 * g;
+        const int32_t kb = k0 + kk0;   // k0 and nout are multiples of 8: one bin per group
+        const int bin = kb / o.nout;
+        const int r0 = kb - bin * o.nout;
+        const float4 ub = o.bin_ubar[bin];
+        const int2 sm = o.bin_samp[bin];
+        const float4 ch = o.chan[r0];
+        const float Xbar = dot3(ub, L);
+        float re[8], im[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
+        for (int s = 0; s < sm.y; ++s) {
+            const float4 d = o.samp[sm.x + s];
+            const float ds = dot3(d, L);
+            const float Xs = Xbar + ds;
+            const float f = dirichlet_fast(o.favg, ch.z * Xs * kInvC) * sincpi_fast(ch.w * Xs * kInvC);
+            float es, ec, rs, rc;
+            sincospi2_fast(-ch.x * ds * kInvC, &es, &ec);
+            sincospi2_fast(-o.dnu_ch * ds * kInvC, &rs, &rc);
+            float er = ec * f, ei = es * f;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                re[j] += er;
+                im[j] += ei;
+                const float t = er * rc - ei * rs;
+                ei = er * rs + ei * rc;
+                er = t;
+            }
+        }
+        const float inv = 1.0f / (float)sm.y;
+        float2 *dst = w + (int64_t)p * ldw + kk0;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float Wk = (kk0 + j < kn) ? o.W[kb + j] : 0.f;
+            if (kk0 + j < kn) dst[j] = make_float2(Wk * re[j] * inv, Wk * im[j] * inv);
+        }
+    }
+}
+
 cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const float4 *pos, int npos,
                            int32_t k0, int32_t kn, float2 *w, int64_t ldw, int fast, cudaStream_t st) {
     if (npos <= 0 || kn <= 0) return cudaSuccess;
@@ -51,6 +99,11 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
     }
     const int64_t blocks = std::min<int64_t>((kn + 255) / 256, (int64_t)nsm * 16 / std::max(1, std::min(npos, 16)));
     dim3 grid((unsigned)std::max<int64_t>(1, blocks), npos);
+    if (fast && method == kExact && o.chan_affine && o.nout % 8 == 0 && k0 % 8 == 0) {
+        const int64_t b8 = std::min<int64_t>((kn / 8 + 255) / 256 + 1, (int64_t)nsm * 16 / std::max(1, std::min(npos, 16)));
+        k_weights_exact8<<<dim3((unsigned)std::max<int64_t>(1, b8), npos), 256, 0, st>>>(o, pos, k0, kn, w, ldw);
+        return cudaGetLastError();
+    }
     if (fast) k_weights<true><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
     else k_weights<false><<<grid, 256, 0, st>>>(o, method, flags, pos, k0, kn, w, ldw);
     return cudaGetLastError();
