@@ -4,8 +4,8 @@ Workload (default): the MeerKAT-shaped single cutout -- 64 antennas (32 within
 1 km, 32 within 8 km; 2016 baselines), 4 h of 1 s samples averaged 8:1, 16
 channels of 0.836 MHz from 856 MHz (58 060 800 averaged visibilities), one
 128 x 128 cutout at 1.5 arcsec around (l0, m0) = (0.03, 0.03).  One step
-evaluates the exact smeared PSF and both approximations (psf_exact,
-psf_approx_uv, psf_approx_img) on the tensor cores.
+evaluates the exact smeared PSF and both approximations (psf_exact and
+psf_approx_uv_img, which computes Methods 1 and 2 in one pass) on the tensor cores.
 
 Metric: px.vis terms per second, one term = one (output pixel, averaged
 visibility) pair (4 real flops of the complex contraction).  `value` is the
@@ -37,8 +37,9 @@ import obsgen  # noqa: E402
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}
 # DRAM bytes (read + write) per contraction launch from the ncu capture summarised in
 # profiles/k_psf_tc_meerkat64_1h_128px.md, per visibility (traffic is proportional to
-# K), valid only for the kernel source it was taken on.
-PROFILED_TRAFFIC = {"kernel_sha256_prefix": "4ecdc63840e7f1e8", "bytes_per_vis": (232.441088e6 + 3.470848e6) / 14515200,
+# K; the mean of the step's two launches: exact, fused uv + img), valid only for the
+# kernel source it was taken on.
+PROFILED_TRAFFIC = {"kernel_sha256_prefix": None, "bytes_per_vis": None,
                     "profile": "profiles/k_psf_tc_meerkat64_1h_128px.md"}
 
 
@@ -46,7 +47,7 @@ def profiled_traffic(nvis):
     import hashlib
     src = os.path.join(ROOT, "paper_2009_07010_gb300", "csrc", "k_tc.cu")
     h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    if h != PROFILED_TRAFFIC["kernel_sha256_prefix"]:
+    if h != PROFILED_TRAFFIC["kernel_sha256_prefix"] or PROFILED_TRAFFIC["bytes_per_vis"] is None:
         return None
     return PROFILED_TRAFFIC["bytes_per_vis"] * nvis
 WORKLOAD = "meerkat64_4h_16ch_128px_single_cutout"
@@ -183,6 +184,11 @@ def parity_check(psf):
             for m in ("exact", "uv", "img"):
                 got = plan.forward(m, batch).cpu().numpy().astype(np.float64)
                 res[f"{prec}/{m}"] = float(np.max(np.abs(got - refs[m])) / np.max(np.abs(refs[m])))
+            # the fused call of the benchmark step (both approximations in one pass)
+            guv, gimg = plan.approx_uv_img(batch)
+            for m, got in (("uv", guv), ("img", gimg)):
+                got = got.cpu().numpy().astype(np.float64)
+                res[f"{prec}/{m}_fused"] = float(np.max(np.abs(got - refs[m])) / np.max(np.abs(refs[m])))
     return {"workload": "16ant_1km_1h_4ch_64px", "metric": "max |P - P_oracle| / max |P_oracle|", "err_max": res,
             "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3}}
 
@@ -379,8 +385,7 @@ def main():
 
     def step(p):
         p.exact(batch, out=outs[0])
-        p.approx_uv(batch, out=outs[1])
-        p.approx_img(batch, out=outs[2])
+        p.approx_uv_img(batch, out_uv=outs[1], out_img=outs[2])
 
     for _ in range(args.warmup):
         step(plan)
@@ -463,13 +468,18 @@ def main():
         peak = peaks.get("bf16_tflops", FALLBACK_PEAKS["bf16_tflops"])
         launches = max(nkc, 1)
         avg_ms = kms / launches
-        flops_launch = 4.0 * K * batch.total()
-        achieved = flops_launch / (avg_ms * 1e-3) / 1e12
+        # algorithmic flops of all contraction launches in the timed region: three
+        # methods per step, 4 flops per px.vis term (the exact launch does one method,
+        # the fused launch two)
+        flops_total = 3 * 4.0 * K * batch.total() * args.steps
+        flops_launch = flops_total / launches
+        achieved = flops_total / (kms * 1e-3) / 1e12
         traffic = profiled_traffic(K)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "traffic_unit": "bytes per launch",
                 "traffic_source": PROFILED_TRAFFIC["profile"] if traffic else None, "peak_source": src,
-                "kernel": "k_psf_tc (tcgen05 contraction)", "avg_launch_ms": avg_ms,
+                "kernel": "k_psf_tc (tcgen05 contraction: exact launch + fused uv/img launch per step)",
+                "avg_launch_ms": avg_ms, "launches_per_step": launches / args.steps,
                 "algorithmic_flops_per_launch": flops_launch}
         cpu = None if args.no_cpu_baseline else cpu_baseline_sample(obs, batch_g)
         line = {"metric": "smeared-PSF px.vis terms/sec (exact + uv + img)", "value": value, "unit": "terms/s",

@@ -147,6 +147,16 @@ int psf_approx_uv(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, voi
  * visibility's uv point); same arguments as psf_exact. */
 int psf_approx_img(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
 
+/* Methods 1 and 2 of the same batch in one call (the comparison of both
+ * approximations of Sect. 4): out_uv_dev receives what psf_approx_uv writes and
+ * out_img_dev what psf_approx_img writes (same layout, out_offset and gaps rules,
+ * distinct device float32 buffers).  With a tensor-core precision and cutouts of 64
+ * or 128 pixels that the per-cutout form handles, both outputs come from one pass
+ * that shares the twiddles of the two methods; otherwise the two calls are made in
+ * turn.  Errors as psf_exact; out_uv_dev or out_img_dev NULL -> PSF_EINVAL. */
+int psf_approx_uv_img(psf_plan_t plan, const psf_batch_t *batch, float *out_uv_dev, float *out_img_dev,
+                      void *cuda_stream);
+
 /* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
  * adjoint: given dL/dP (device float32, same layout as the forward output) it
  * writes dL/d(l0,m0) to dL_dlm_dev (device float64 [npos][2], overwritten) and,

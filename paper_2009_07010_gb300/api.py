@@ -112,6 +112,22 @@ class Plan:
     def approx_img(self, batch, out=None, stream=None):
         return self.forward("img", batch, out, stream)
 
+    def approx_uv_img(self, batch: Batch, out_uv: Optional[torch.Tensor] = None,
+                      out_img: Optional[torch.Tensor] = None, stream=None):
+        """Methods 1 and 2 of one batch in one call: (uv cutouts, image-plane cutouts)."""
+        outs = []
+        for o in (out_uv, out_img):
+            if o is None:
+                o = torch.empty(max(batch.total(), 1), dtype=torch.float32, device="cuda")
+            assert o.dtype == torch.float32 and o.is_cuda and o.is_contiguous()
+            assert o.numel() >= batch.total()
+            outs.append(o)
+        bs = batch.struct()
+        check(_lib.lib().psf_approx_uv_img(self._h, ctypes.byref(bs), ctypes.c_void_p(outs[0].data_ptr()),
+                                           ctypes.c_void_p(outs[1].data_ptr()), _stream_handle(stream)),
+              "psf_approx_uv_img")
+        return outs[0], outs[1]
+
     def adjoint(self, method: str, batch: Batch, dL_dP: torch.Tensor, want_dW: bool = True, stream=None):
         """(dL/d(l0,m0) float64 [npos,2], dL/dW float32 [nvis] or None) on the device."""
         assert dL_dP.dtype == torch.float32 and dL_dP.is_cuda and dL_dP.is_contiguous()

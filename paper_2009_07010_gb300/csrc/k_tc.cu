@@ -145,6 +145,70 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
     }
 }
 
+// Two real-weight copies of one conjugate-symmetric 32-row chain of unweighted twiddles
+// (the fused uv + image-plane form): the value z(r) of row R0 + r is stored as
+// (wa z) at base + r rows and (wb z) at base + half_off + r rows, each with its
+// conjugate at the mirrored row R0 - r (mbase, mbase + half_off); with `tail` the
+// conjugates of (wa, wb) x the value one step past the last row go to row 0 of each
+// half (tail_addr, tail_addr + half_off).
+template <int BF16>
+__device__ __forceinline__ void gen_chain32_dual(uint32_t base, uint32_t mbase, uint32_t half_off, float theta,
+                                                 int n0, float wa, float wb, bool tail, uint32_t tail_addr) {
+    const float2 st = cis_turns(theta);
+    float2 z[8];
+    z[0] = cis_turns(theta * (float)n0);
+    const float2 s2 = cmulf(st, st), s4 = cmulf(s2, s2), s8 = cmulf(s4, s4), s16 = cmulf(s8, s8);
+    z[1] = cmulf(z[0], s4);
+    z[2] = cmulf(z[0], s8);
+    z[3] = cmulf(z[1], s8);
+#pragma unroll
+    for (int pc = 4; pc < 8; ++pc) z[pc] = cmulf(z[pc - 4], s16);
+    float2 re[4], im[4];
+    re[0] = make_float2(z[0].x, z[4].x); im[0] = make_float2(z[0].y, z[4].y);
+    re[1] = make_float2(z[2].x, z[6].x); im[1] = make_float2(z[2].y, z[6].y);
+    re[2] = make_float2(z[1].x, z[5].x); im[2] = make_float2(z[1].y, z[5].y);
+    re[3] = make_float2(z[3].x, z[7].x); im[3] = make_float2(z[3].y, z[7].y);
+    const float2 sr = make_float2(st.x, st.x), si = make_float2(st.y, st.y), nsi = make_float2(-st.y, -st.y);
+    constexpr uint32_t kConj = 0x80000000u;
+    const uint32_t ln = threadIdx.x & 31u, ca = ln & 7u;
+    const uint32_t lrow = (((threadIdx.x >> 3) & 3u) << 10);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 wv = h ? make_float2(wb, wb) : make_float2(wa, wa);
+            const uint32_t ho = h ? half_off : 0u;
+#pragma unroll
+            for (int m = 0; m < 2; ++m) {   // matrices of rows q + 8 m' (m = 0) and q + 4 + 8 m' (m = 1)
+                const float2 ra = __fmul2_rn(re[2 * m], wv), ia = __fmul2_rn(im[2 * m], wv);
+                const float2 rb = __fmul2_rn(re[2 * m + 1], wv), ib = __fmul2_rn(im[2 * m + 1], wv);
+                const uint32_t v0 = pack2<BF16>(ra.x, ia.x), v1 = pack2<BF16>(rb.x, ib.x);
+                const uint32_t v2 = pack2<BF16>(ra.y, ia.y), v3 = pack2<BF16>(rb.y, ib.y);
+                const uint32_t qq = (uint32_t)(q + 4 * m);
+                stmatrix_x4(base + ho + lrow + qq * 128u + ((ca ^ qq) << 4), v0, v1, v2, v3);
+                stmatrix_x4(mbase + ho - lrow - qq * 128u + ((ca ^ ((8u - qq) & 7u)) << 4), v0 ^ kConj, v1 ^ kConj,
+                            v2 ^ kConj, v3 ^ kConj);
+            }
+        }
+        if (q < 3) {
+#pragma unroll
+            for (int pp = 0; pp < 4; ++pp) {
+                const float2 t = __fmul2_rn(im[pp], nsi), u = __fmul2_rn(im[pp], sr);
+                im[pp] = __ffma2_rn(re[pp], si, u);
+                re[pp] = __ffma2_rn(re[pp], sr, t);
+            }
+        }
+    }
+    if (tail) {   // row 32 = piece 7 (row 31, the .y half of pair 3) one step on
+        const float r32 = re[3].y * st.x - im[3].y * st.y, i32 = re[3].y * st.y + im[3].y * st.x;
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + ln * 4u), "r"(pack2<BF16>(wa * r32, -wa * i32))
+                     : "memory");
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + half_off + ln * 4u),
+                     "r"(pack2<BF16>(wb * r32, -wb * i32))
+                     : "memory");
+    }
+}
+
 struct SmemLayout {
     uint32_t a_off, b_off, in_off, bar_off, bytes;
 };
@@ -157,13 +221,13 @@ __host__ __device__ constexpr int stages_for(int ncols_max) {
     return ncols_max > 128 ? 4 : (ncols_max > 64 ? 6 : 8);
 }
 
-__host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
+__host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages, uint32_t in_slot = kInSlotBytes) {
     SmemLayout L;
     const uint32_t bt = (uint32_t)ncols_max * 128u;
     L.a_off = 0;
     L.b_off = kStages * kATileBytes;
     L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
-    L.bar_off = L.in_off + kInStages * kInSlotBytes;
+    L.bar_off = L.in_off + kInStages * in_slot;
     L.bytes = L.bar_off + 512;   // 2 S + 2 kInStages + 8 barriers (<= 56 x 8 B), TMEM address, abort flag
     return L;
 }
@@ -171,16 +235,23 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages) {
 // MIR: 1 = the weights of the launch are real, so whole-cutout tiles may use the
 // conjugate-symmetric generation (a separate instance keeps its register pressure out
 // of the complex-weight kernel); 2 = real weights and every tile of the launch spans
-// a whole 64- or 128-pixel cutout (no unmirrored path compiled in).
+// a whole 64- or 128-pixel cutout (no unmirrored path compiled in); 4 = the fused uv +
+// image-plane form on such tiles: the A operand holds the unweighted column twiddles,
+// the B operand (2 N rows) the row twiddles times the Method 1 weights (rows 0 .. N-1)
+// and times the Method 2 weights (rows N .. 2N-1), so one N = 2 ncols MMA yields both
+// cutouts side by side in TMEM (w2: second weight rows; part2: offset of the second
+// cutout's partial sums from `partial`).
 template <int BF16, int kStages, int NISS, int MIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
              const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
-             int64_t split_stride, int *err) {
+             int64_t split_stride, int *err, const float2 *__restrict__ w2, int64_t part2) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the operand tiles (swizzle atoms)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    const SmemLayout L = smem_layout(ncols_max, kStages);
+    constexpr int kBMul = (MIR == 4) ? 2 : 1;                       // B rows per output column
+    constexpr uint32_t kSlot = (MIR == 4) ? kKS * 24 : kInSlotBytes;   // uv, w (, w2) per visibility
+    const SmemLayout L = smem_layout(kBMul * ncols_max, kStages, kSlot);
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
     uint64_t *empty = full + kStages;
     uint64_t *in_full = empty + kStages;
@@ -195,8 +266,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     const TcItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncols = it.ncols;
-    const uint32_t bt_stride = ((uint32_t)ncols_max * 128u + 1023u) / 1024u * 1024u;
-    const uint32_t acc_cols = pow2_cols(ncols_max);
+    const uint32_t bt_stride = ((uint32_t)(kBMul * ncols_max) * 128u + 1023u) / 1024u * 1024u;
+    const uint32_t acc_cols = pow2_cols(kBMul * ncols_max);
     const int nst = (it.k1 - it.k0 + kKS - 1) / kKS;
 
     if (threadIdx.x == 0) {
@@ -234,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // a tile that spans a whole cutout of 64 or 128 pixels only rows N/2 .. N-1 are
         // generated; rows 1 .. N/2 are their conjugates and row 0 the conjugate of the
         // value one step past row N-1.
-        const bool mirror = (MIR == 2) || (MIR == 1 && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0);
+        const bool mirror = (MIR == 2) || (MIR == 4) || (MIR == 1 && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0);
         const int nA = mirror ? it.N / 64 : 4;            // 32-row chains of the A (128 rows) and B tiles
         const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
@@ -245,9 +316,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int islot = s_i % kInStages;
             bool ok = wait_bounded(&in_full[islot], (uint32_t)(s_i / kInStages) & 1u, s_abort, err);
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
-            const float2 *in_uv = (const float2 *)(smem + L.in_off + islot * kInSlotBytes);
+            const float2 *in_uv = (const float2 *)(smem + L.in_off + islot * kSlot);
             const float2 uvk = in_uv[lane];
-            const float2 wk = (it.k0 + s_i * kKS + lane < it.k1) ? in_uv[kKS + lane] : make_float2(0.f, 0.f);
+            const bool kin = it.k0 + s_i * kKS + lane < it.k1;
+            const float2 wk = kin ? in_uv[kKS + lane] : make_float2(0.f, 0.f);
+            const float w2k = (MIR == 4 && kin) ? in_uv[2 * kKS + lane].x : 0.f;
             __syncwarp();
             if (lane == 0) mbar_arrive(&in_empty[islot]);   // the input slot may be refilled
             if (s_i >= kStages) {
@@ -257,7 +330,18 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kATileBytes);
             const uint32_t b_tile = smem_u32(smem + L.b_off + slot * bt_stride);
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
-                if (mirror) {   // rows R0 .. R0+31 (R0 = N/2 + 32 c) and their mirrors N - R0 - r
+                if (MIR == 4) {   // A: unweighted column twiddles; B: weighted row twiddles, both halves
+                    const bool isA = ch < nA;
+                    const int c = isA ? ch : ch - nA;
+                    const int R0 = half + 32 * c;
+                    if (isA)
+                        gen_chain32<BF16, true>(a_tile + (uint32_t)R0 * 128u, off8, uvk.y * cell, 32 * c, wk, false,
+                                                a_tile + (uint32_t)(it.N - R0) * 128u, c == nA - 1, a_tile);
+                    else
+                        gen_chain32_dual<BF16>(b_tile + (uint32_t)R0 * 128u, b_tile + (uint32_t)(it.N - R0) * 128u,
+                                               (uint32_t)it.N * 128u, -uvk.x * cell, 32 * c, wk.x, w2k, c == nB - 1,
+                                               b_tile);
+                } else if (mirror) {   // rows R0 .. R0+31 (R0 = N/2 + 32 c) and their mirrors N - R0 - r
                     const bool isA = ch < nA;
                     const int c = isA ? ch : ch - nA;
                     const int R0 = half + 32 * c;
@@ -287,7 +371,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             // instruction, so the per-stage path is kept short: slot, phase and range
             // by increment, descriptors by adding the slot offset to the 14-bit address
             // field (shared addresses < 256 KB cannot carry out of it).
-            const uint32_t idesc = idesc_f16(128, ncols, BF16);
+            const uint32_t idesc = idesc_f16(128, kBMul * ncols, BF16);
             const uint64_t ad0 = desc_sw128(smem_u32(smem + L.a_off));
             const uint64_t bd0 = desc_sw128(smem_u32(smem + L.b_off));
             int slot = q, r = q, d = 0;
@@ -339,11 +423,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (s_i >= kInStages &&
                     !wait_bounded(&in_empty[islot], (uint32_t)(s_i / kInStages - 1) & 1u, s_abort, err))
                     break;
-                uint8_t *dst = smem + L.in_off + islot * kInSlotBytes;
+                uint8_t *dst = smem + L.in_off + islot * kSlot;
                 const int32_t kb = it.k0 + s_i * kKS;
-                mbar_arrive_expect_tx(&in_full[islot], kInSlotBytes);
+                mbar_arrive_expect_tx(&in_full[islot], kSlot);
                 bulk_g2s(dst, uv + kb, kKS * 8, &in_full[islot]);
                 bulk_g2s(dst + kKS * 8, wp + kb, kKS * 8, &in_full[islot]);
+                if (MIR == 4) bulk_g2s(dst + kKS * 16, w2 + (int64_t)it.slot * ldw + kb, kKS * 8, &in_full[islot]);
                 issued = s_i + 1;
             }
             // every copy has landed before the CTA exits (the last use of each slot)
@@ -351,6 +436,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 wait_bounded(&in_full[s_i % kInStages], (uint32_t)(s_i / kInStages) & 1u, &no_abort, err);
         }
         __syncwarp();
+    } else if (warp == kMma2Warp) {
+        // second issuer, idle with one issuer (NISS == 1): it must not join the drain
+        // warps (lane quarters 0-3, four arrivals per accumulator release)
     } else {
         // ------------------------------------------------------------ drain
         // The partial cutout is stored transposed (element (j, i) at i N + j), so the 32
@@ -362,9 +450,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int64_t cstride = it.N;
         const bool row_ok = j < it.N;
         const int ncol_valid = min(ncols, it.N - it.i0);
+        float *dst2 = dst + part2;   // second cutout of the fused form
         if (nst == 0) {
             if (row_ok)
-                for (int c = 0; c < ncol_valid; ++c) dst[c * cstride] = 0.f;
+                for (int c = 0; c < ncol_valid; ++c) {
+                    dst[c * cstride] = 0.f;
+                    if (MIR == 4) dst2[c * cstride] = 0.f;
+                }
         }
         const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
         for (int d = 0; d < ndrain; ++d) {
@@ -376,7 +468,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
             tc_fence_after();
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * acc_cols;
-            for (int c0 = 0; c0 < ncols; c0 += 16) {
+            for (int c0 = 0; c0 < kBMul * ncols; c0 += 16) {
+                // fused form: columns ncols .. 2 ncols - 1 are the second cutout
+                float *const dd = (MIR == 4 && c0 >= ncols) ? dst2 : dst;
+                const int cb = (MIR == 4 && c0 >= ncols) ? c0 - ncols : c0;
                 float v[16];
                 tmem_ld16(ta + (uint32_t)c0, v);
                 if (two) {
@@ -392,10 +487,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                         float o[8];
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            o[e] = (d > 0 && c0 + h + e < ncol_valid) ? dst[(c0 + h + e) * cstride] : 0.f;
+                            o[e] = (d > 0 && cb + h + e < ncol_valid) ? dd[(cb + h + e) * cstride] : 0.f;
 #pragma unroll
                         for (int e = 0; e < 8; ++e)
-                            if (c0 + h + e < ncol_valid) dst[(c0 + h + e) * cstride] = o[e] + v[h + e];
+                            if (cb + h + e < ncol_valid) dd[(cb + h + e) * cstride] = o[e] + v[h + e];
                     }
                 }
             }
@@ -513,14 +608,14 @@ int selftest_timeout(int limit_ms) {
 template <int BF16, int S, int NISS, int MIR>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                                int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
-                               cudaStream_t st) {
-    const SmemLayout L = smem_layout(ncols_max, S);
+                               cudaStream_t st, const float2 *w2 = nullptr, int64_t part2 = 0) {
+    const SmemLayout L = smem_layout((MIR == 4 ? 2 : 1) * ncols_max, S, MIR == 4 ? kKS * 24 : kInSlotBytes);
     const size_t bytes = L.bytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
     if (e != cudaSuccess) return e;
     k_psf_tc<BF16, S, NISS, MIR><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial,
-                                                                   split_stride, err);
+                                                                   split_stride, err, w2, part2);
     return cudaGetLastError();
 }
 
@@ -544,6 +639,23 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
     PSF_TC_CASE(0, 4) PSF_TC_CASE(0, 6) PSF_TC_CASE(0, 8) PSF_TC_CASE(1, 4) PSF_TC_CASE(1, 6) PSF_TC_CASE(1, 8)
 #undef PSF_TC_CASE
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_psf_tc_uvimg(const DevObs &o, const float2 *w_uv, const float2 *w_img, int64_t ldw,
+                                const TcItem *items, int nitems, int ncols_max, int bf16, float cell, float *partial,
+                                int64_t split_stride, int64_t part2, int *err, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    if (ncols_max != 64 && ncols_max != 128) return cudaErrorInvalidValue;
+    // B tiles of 2 ncols rows: 128 rows -> 6 stages, two issuers; 256 rows -> 4 stages, one
+    if (ncols_max == 64)
+        return bf16 ? launch_tc_t<1, 6, 2, 4>(o, w_uv, ldw, items, nitems, 64, cell, partial, split_stride, err, st,
+                                              w_img, part2)
+                    : launch_tc_t<0, 6, 2, 4>(o, w_uv, ldw, items, nitems, 64, cell, partial, split_stride, err, st,
+                                              w_img, part2);
+    return bf16 ? launch_tc_t<1, 4, 1, 4>(o, w_uv, ldw, items, nitems, 128, cell, partial, split_stride, err, st,
+                                          w_img, part2)
+                : launch_tc_t<0, 4, 1, 4>(o, w_uv, ldw, items, nitems, 128, cell, partial, split_stride, err, st,
+                                          w_img, part2);
 }
 
 int selftest_umma(const void *a, const void *b, float *d, int n) {

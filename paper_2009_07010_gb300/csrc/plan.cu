@@ -713,6 +713,115 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
     return PSF_OK;
 }
 
+// Methods 1 and 2 of one batch in one pass (tensor-core precisions, cutouts of 64 or
+// 128 pixels that the per-cutout form computes): the fused kernel shares the twiddles
+// of both methods and writes both cutouts.  Any other batch (the FP32 precision,
+// other sizes, groups large enough for the batched form, PSF_ALGO_CUTOUT off) takes
+// the two separate calls.
+int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float *out_img, cudaStream_t st) {
+    if (!p || !out_uv || !out_img) return PSF_EINVAL;
+    const bool tc = p->opts.prec != PSF_FP32;
+    BatchHost h;
+    int s = prepare_batch(p, b, h, tc ? 256 : 4096);
+    if (s || h.npos == 0) return s;
+    bool fused = tc;
+    int n64 = 0, n128 = 0;
+    for (int i = 0; i < h.npos && fused; ++i) {
+        if (h.npix[i] == 64) ++n64;
+        else if (h.npix[i] == 128) ++n128;
+        else fused = false;
+    }
+    if (fused && p->opts.algo == PSF_ALGO_AUTO && (n64 >= kKrMinGroup || n128 >= kKrMinGroup)) fused = false;
+    if (!fused) {
+        s = run_forward(p, kUV, b, out_uv, st);
+        return s ? s : run_forward(p, kImg, b, out_img, st);
+    }
+    const int64_t K = p->nvis;
+    const int chunk = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(h.npos, 32768), kWeightBudget / (K * 16)));
+    for (int c0 = 0; c0 < h.npos; c0 += chunk) {
+        const int cn = std::min(chunk, h.npos - c0);
+        std::vector<int64_t> loc(cn);
+        int64_t chunk_px = 0;
+        int ncols_max = 64;
+        for (int i = 0; i < cn; ++i) {
+            loc[i] = chunk_px;
+            chunk_px += (int64_t)h.npix[c0 + i] * h.npix[c0 + i];
+            ncols_max = std::max(ncols_max, (int)h.npix[c0 + i]);
+        }
+        // one whole-cutout item per position, visibility splits to fill the SMs
+        std::vector<TcItem> base, items;
+        for (int i = 0; i < cn; ++i) {
+            const int N = h.npix[c0 + i];
+            base.push_back(TcItem{i, N, 0, 0, N, 0, 0, 0, loc[i]});
+        }
+        int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((p->nsm + cn - 1) / cn, (K + 8191) / 8192));
+        const int32_t kper = (int32_t)(((K + nsplit - 1) / nsplit + 31) / 32 * 32);
+        nsplit = (int)((K + kper - 1) / kper);
+        for (int sp = 0; sp < nsplit; ++sp)
+            for (auto it : base) {
+                it.k0 = (int32_t)(sp * (int64_t)kper);
+                it.k1 = (int32_t)std::min<int64_t>(K, (int64_t)(sp + 1) * kper);
+                it.split = sp;
+                items.push_back(it);
+            }
+        Meta m;
+        m.off_pos = 0;
+        m.off_npix = align_up(m.off_pos + cn * sizeof(float4), 16);
+        m.off_loc = align_up(m.off_npix + cn * sizeof(int32_t), 16);
+        m.off_out = align_up(m.off_loc + cn * sizeof(int64_t), 16);
+        m.off_tiles = align_up(m.off_out + cn * sizeof(int64_t), 16);
+        const size_t tbytes = items.size() * sizeof(TcItem);
+        m.bytes = align_up(m.off_tiles + tbytes, 16);
+        std::vector<char> blob(m.bytes, 0);
+        std::memcpy(blob.data() + m.off_pos, &h.pos[c0], cn * sizeof(float4));
+        std::memcpy(blob.data() + m.off_npix, &h.npix[c0], cn * sizeof(int32_t));
+        std::memcpy(blob.data() + m.off_loc, loc.data(), cn * sizeof(int64_t));
+        std::memcpy(blob.data() + m.off_out, &h.out_off[c0], cn * sizeof(int64_t));
+        std::memcpy(blob.data() + m.off_tiles, items.data(), tbytes);
+        if ((s = upload_meta(p, blob.data(), m.bytes, st))) return s;
+        char *dm = (char *)p->meta.p;
+        const float4 *d_pos = (const float4 *)(dm + m.off_pos);
+        const int32_t *d_npix = (const int32_t *)(dm + m.off_npix);
+        const int64_t *d_loc = (const int64_t *)(dm + m.off_loc);
+        const int64_t *d_out = (const int64_t *)(dm + m.off_out);
+        // two weight blocks (Method 1, Method 2), rows padded as in run_forward
+        const int64_t ldw = (K + 31) / 32 * 32;
+        const int64_t wblock = cn * ldw + 64;
+        PSF_TRY(p->wbuf.reserve((size_t)(2 * wblock) * sizeof(float2)));
+        float2 *w_uv = (float2 *)p->wbuf.p, *w_img = w_uv + wblock;
+        PSF_TRY(launch_weights(p->d, kUV, p->opts.flags, d_pos, cn, 0, (int32_t)K, w_uv, ldw, 1, st));
+        PSF_TRY(launch_weights(p->d, kImg, p->opts.flags, d_pos, cn, 0, (int32_t)K, w_img, ldw, 1, st));
+        p->n_kernels += 2;
+        const int64_t part2 = (int64_t)nsplit * chunk_px;
+        PSF_TRY(p->partial.reserve((size_t)(2 * part2) * sizeof(float)));
+        float *part = (float *)p->partial.p;
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        if (p->prof) {
+            if (p->prof_used == p->prof_ev.size()) {
+                cudaEvent_t a, c;
+                PSF_TRY(cudaEventCreate(&a));
+                PSF_TRY(cudaEventCreate(&c));
+                p->prof_ev.emplace_back(a, c);
+            }
+            ev1 = p->prof_ev[p->prof_used].first;
+            ev2 = p->prof_ev[p->prof_used].second;
+            p->prof_used++;
+            PSF_TRY(cudaEventRecord(ev1, st));
+        }
+        PSF_TRY(launch_psf_tc_uvimg(p->d, w_uv, w_img, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(),
+                                    ncols_max, p->opts.prec == PSF_TC_BF16, (float)h.cell, part, chunk_px, part2,
+                                    (int *)p->err.p, st));
+        if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+        p->n_contract++;
+        p->n_kernels++;
+        PSF_TRY(launch_reduce(part, nsplit, chunk_px, d_loc, d_out, d_npix, cn, 1, out_uv, st));
+        PSF_TRY(launch_reduce(part + part2, nsplit, chunk_px, d_loc, d_out, d_npix, cn, 1, out_img, st));
+        p->n_kernels += 2;
+    }
+    return PSF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -725,6 +834,9 @@ int psf_approx_uv(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) 
 }
 int psf_approx_img(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
     return run_forward(p, kImg, b, out, (cudaStream_t)stream);
+}
+int psf_approx_uv_img(psf_plan_t p, const psf_batch_t *b, float *out_uv, float *out_img, void *stream) {
+    return run_forward_uvimg(p, b, out_uv, out_img, (cudaStream_t)stream);
 }
 
 int psf_adjoint(psf_plan_t p, int method, const psf_batch_t *b, const float *dLdP, double *dLdlm, float *dLdW,

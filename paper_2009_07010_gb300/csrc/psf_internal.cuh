@@ -88,6 +88,12 @@ struct TcItem {
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items,
                           int nitems, int ncols_max, int bf16, float cell, int wreal, float *partial,
                           int64_t split_stride, int *err_flag, cudaStream_t st);
+// Fused Methods 1 + 2 on whole cutouts of 64 or 128 pixels (every item: i0 = j0 = 0,
+// ncols = N; ncols_max 64 or 128): partial sums of the uv cutouts at `partial` and of
+// the image-plane cutouts at partial + part2, both laid out like launch_psf_tc's.
+cudaError_t launch_psf_tc_uvimg(const DevObs &o, const float2 *w_uv, const float2 *w_img, int64_t ldw,
+                                const TcItem *items, int nitems, int ncols_max, int bf16, float cell, float *partial,
+                                int64_t split_stride, int64_t part2, int *err, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
 int selftest_timeout(int limit_ms);
 

@@ -46,6 +46,7 @@ def test_null_handles(L):
     b = _lib.BatchT(0, None, None, 0, 1e-5, None)
     for fn in (L.psf_exact, L.psf_approx_uv, L.psf_approx_img):
         assert fn(None, ctypes.byref(b), None, None) == _lib.PSF_EINVAL
+    assert L.psf_approx_uv_img(None, ctypes.byref(b), None, None, None) == _lib.PSF_EINVAL
     assert L.psf_adjoint(None, 0, ctypes.byref(b), None, None, None, None) == _lib.PSF_EINVAL
     assert L.psf_sync_status(None, None) == _lib.PSF_EINVAL
     assert L.psf_plan(None, None, None) == _lib.PSF_EINVAL
