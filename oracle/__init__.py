@@ -130,8 +130,11 @@ def _batch_arrays(batch, offsets=None):
     return lm, npix, offsets, total
 
 
-def psf(obs, method: int, batch, flags: int = 0, pix_sel=None, offsets=None) -> np.ndarray:
-    """Packed cutouts (float64).  With pix_sel, only those packed indices are filled (rest NaN)."""
+def psf(obs, method: int, batch, flags: int = 0, pix_sel=None, offsets=None, imag: bool = False) -> np.ndarray:
+    """Packed cutouts (float64): the real part of the sum of Eqs. 21-22, or with imag=True
+    its imaginary part.  With pix_sel, only those packed indices are filled (rest NaN)."""
+    if imag:
+        flags = int(flags) | 8
     o = _Obs(obs)
     lm, npix, offs, total = _batch_arrays(batch, offsets)
     out = np.full(total, np.nan)

@@ -29,8 +29,10 @@ def _gl_nodes(n: int):
 
 
 def psf_exact(obs, l0: float, m0: float, npix: int, cell: float, wterm: bool = False,
-              nquad: int = 24) -> np.ndarray:
-    """Cutout [npix, npix] (row j = m offset, column i = l offset) in longdouble."""
+              nquad: int = 24, imag: bool = False) -> np.ndarray:
+    """Cutout [npix, npix] (row j = m offset, column i = l offset) in longdouble: the
+    real part of the sum over averaged visibilities, or with imag=True its imaginary
+    part."""
     ld = np.longdouble
     uvw = obs.uvw_m.astype(ld)
     freq = obs.freq_hz.astype(ld)
@@ -69,6 +71,9 @@ def psf_exact(obs, l0: float, m0: float, npix: int, cell: float, wterm: bool = F
                 u = ubar * nu_r / C_LIGHT
                 W = ld(obs.weights[k]) if obs.weights is not None else ld(n * favg)
                 ph = TWO_PI * (u[0] * L + u[1] * M + u[2] * n0m1)
-                out += W * (vis_re * np.cos(ph) - vis_im * np.sin(ph))
+                if imag:
+                    out += W * (vis_re * np.sin(ph) + vis_im * np.cos(ph))
+                else:
+                    out += W * (vis_re * np.cos(ph) - vis_im * np.sin(ph))
                 k += 1
     return out

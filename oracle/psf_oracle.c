@@ -277,6 +277,10 @@ int or_psf(OR_OBS_ARGS, int method, int npos, const double *lm, const int *npix,
            int64_t nsel, const int64_t *pix_sel) {
     or_obs o = OR_OBS_INIT;
     int64_t nvis;
+    /* flag bit 8: the imaginary part of the (complex) sum of Eqs. 21-22 instead of
+     * the real part; the other bits go to the decorrelation */
+    const int imag = (flags & 8) != 0;
+    flags &= ~8;
     or_vis *v = or_make_vis(&o, &nvis);
     if (!v) return -1;
     double *Dre = (double *)malloc(sizeof(double) * nvis), *Dim = (double *)malloc(sizeof(double) * nvis);
@@ -302,7 +306,8 @@ int or_psf(OR_OBS_ARGS, int method, int npos, const double *lm, const int *npix,
                 double dl = (i - N / 2) * cell, dm = (j - N / 2) * cell, acc = 0;
                 for (int64_t k = 0; k < nvis; ++k) {
                     double ph = 2 * OR_PI * (uu[k] * dl + vv[k] * dm);
-                    acc += v[k].W * (Dre[k] * cos(ph) - Dim[k] * sin(ph));
+                    acc += imag ? v[k].W * (Dre[k] * sin(ph) + Dim[k] * cos(ph))
+                                : v[k].W * (Dre[k] * cos(ph) - Dim[k] * sin(ph));
                 }
                 out[g] = acc;
             }
@@ -313,7 +318,8 @@ int or_psf(OR_OBS_ARGS, int method, int npos, const double *lm, const int *npix,
                 double dl = (i - N / 2) * cell, dm = (j - N / 2) * cell, acc = 0;
                 for (int64_t k = 0; k < nvis; ++k) {
                     double ph = 2 * OR_PI * (uu[k] * dl + vv[k] * dm);
-                    acc += v[k].W * (Dre[k] * cos(ph) - Dim[k] * sin(ph));
+                    acc += imag ? v[k].W * (Dre[k] * sin(ph) + Dim[k] * cos(ph))
+                                : v[k].W * (Dre[k] * cos(ph) - Dim[k] * sin(ph));
                 }
                 out[off + loc] = acc;
             }

@@ -154,6 +154,40 @@ def test_p4_real_decorrelation_gives_centrosymmetric_cutout(method):
     np.testing.assert_allclose(inner, inner[::-1, ::-1], rtol=0, atol=1e-10 * abs(P).max())
 
 
+def test_p4_imaginary_part_flips_under_mirroring():
+    """The imaginary part of the complex sum (PSF_COMPLEX_OUT): the mirrored array
+    measures conjugate visibilities, so its imaginary cutout is the negative of the
+    original for every method (D(-uvw) = conj D(uvw), conj twiddles)."""
+    obs = obsgen.tiny_obs()
+    mir = obsgen.Observation(-obs.uvw_m, obs.time_s, obs.freq_hz, obs.chan_width_hz,
+                             obs.tavg, obs.favg)
+    b = obsgen.Batch(np.array([[0.04, 0.01]]), np.array([12], np.int32), 3e-5)
+    for method in range(3):
+        im = oracle.psf(obs, method, b, imag=True)
+        im_m = oracle.psf(mir, method, b, imag=True)
+        assert np.max(np.abs(im)) > 1e-3 * np.max(np.abs(oracle.psf(obs, method, b)))
+        np.testing.assert_allclose(im_m, -im, rtol=0, atol=1e-10 * np.max(np.abs(im)))
+
+
+def test_p1_imaginary_part_at_zero_smearing():
+    """With D = 1 (phase centre) the imaginary part is sum_k W_k sin(2 pi (u_k dl + v_k dm)):
+    on a uv grid commensurate with the cutout it is the imaginary part of numpy's
+    ifft2 of the gridded weights."""
+    N, cell = 16, 1e-4
+    du = 1.0 / (N * cell)
+    rng = np.random.default_rng(5)
+    a = rng.integers(-7, 8, size=9)
+    bb = rng.integers(-7, 8, size=9)
+    obs = _static_obs(list(zip(a * du, bb * du)), 1.0e9)
+    obs.weights = rng.uniform(0.5, 2.0, size=9).astype(np.float32)
+    P = oracle.psf(obs, oracle.EXACT, obsgen.Batch(np.zeros((1, 2)), np.array([N], np.int32), cell), imag=True)
+    G = np.zeros((N, N), complex)
+    for k in range(9):
+        G[bb[k] % N, a[k] % N] += obs.weights[k]
+    ref = np.fft.fftshift(np.imag(np.fft.ifft2(G)) * N * N)
+    np.testing.assert_allclose(P.reshape(N, N), ref, rtol=0, atol=1e-10)
+
+
 # ----------------------------------------------------------------- P5
 def test_p5_linear_in_weights():
     obs1 = obsgen.tiny_obs(weights=True)
@@ -181,6 +215,11 @@ def test_p6_bruteforce_undivided(wterm):
         got = oracle.psf(obs, oracle.EXACT, obsgen.Batch(np.array([[l0, m0]]), np.array([N], np.int32),
                                                          cell), flags=oracle.WTERM if wterm else 0)
         np.testing.assert_allclose(got.reshape(N, N), ref, rtol=0, atol=1e-11 * abs(ref).max())
+        # the imaginary part along the same undivided route
+        ref_i = brute.psf_exact(obs, l0, m0, N, cell, wterm=wterm, imag=True).astype(np.float64)
+        got_i = oracle.psf(obs, oracle.EXACT, obsgen.Batch(np.array([[l0, m0]]), np.array([N], np.int32), cell),
+                           flags=oracle.WTERM if wterm else 0, imag=True)
+        np.testing.assert_allclose(got_i.reshape(N, N), ref_i, rtol=0, atol=1e-11 * abs(ref).max())
 
 
 # ----------------------------------------------------------------- P7
