@@ -59,6 +59,19 @@ extern "C" {
 /* ---- option flags ------------------------------------------------------ */
 #define PSF_WTERM             1u  /* use L0 = (l0, m0, n0-1): w enters the smearing */
 #define PSF_IMG_LITERAL_THETA 2u  /* Method 2 with theta = arctan(u/v) as printed   */
+/* Bitwise reproducible results run to run on the same device and library build: the
+ * batched form (whose output adds the visibility splits with atomics, in arrival
+ * order) is not used; every cutout takes the per-cutout form, whose split partials
+ * are summed in float64 in a fixed order.  The adjoint is deterministic anyway. */
+#define PSF_DETERMINISTIC     4u
+/* Complex cutouts: each cutout takes 2 N^2 floats, the N^2 real parts (the default
+ * output) followed by the N^2 imaginary parts of sum_k W_k D_k exp(2 pi i (u_k dl +
+ * v_k dm)) (Eqs. 21-22 before taking the real part; the imaginary part is what the
+ * Hermitian conjugate baselines would cancel).  Packed default offsets advance by
+ * 2 N^2; caller-given offsets must leave 2 N^2 floats per cutout.  Tensor-core
+ * precisions and N <= 128 only (PSF_EUNSUPPORTED otherwise); computed by the
+ * per-cutout form.  psf_adjoint and psf_exact_noalloc ignore the flag (real parts). */
+#define PSF_COMPLEX_OUT       8u
 
 /* ---- contraction algorithm (psf_opts_t.algo) ---------------------------- */
 #define PSF_ALGO_AUTO 0   /* per-cutout form for small batches, batched otherwise */
@@ -96,7 +109,7 @@ typedef struct {
 } psf_obs_t;
 
 /* prec: PSF_FP32 / PSF_TC_FP16 / PSF_TC_BF16.  flags: PSF_WTERM |
- * PSF_IMG_LITERAL_THETA.  algo: PSF_ALGO_*. */
+ * PSF_IMG_LITERAL_THETA | PSF_DETERMINISTIC | PSF_COMPLEX_OUT.  algo: PSF_ALGO_*. */
 typedef struct {
     int32_t prec;
     uint32_t flags;
@@ -136,8 +149,9 @@ int psf_plan_set_opts(psf_plan_t plan, const psf_opts_t *opts);
 int64_t psf_plan_nvis(psf_plan_t plan);
 
 /* Exact smeared PSF cutouts (Eqs. 13, 21-22).  out_dev: device float32 buffer
- * of at least max(offset_p + N_p^2) floats, fully overwritten on the cutouts'
- * pixels.  PSF_EUNSUPPORTED if a tensor-core precision is requested for N > 256. */
+ * of at least max(offset_p + N_p^2) floats (2 N_p^2 with PSF_COMPLEX_OUT), fully
+ * overwritten on the cutouts' pixels.  PSF_EUNSUPPORTED if a tensor-core precision
+ * is requested for N > 256 (N > 128 with PSF_COMPLEX_OUT). */
 int psf_exact(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
 
 /* Method 1, uv-plane approximation (Eqs. 31-35); same arguments as psf_exact. */

@@ -52,10 +52,15 @@ class Batch:
     def from_obsgen(cls, b):
         return cls(b.lm, b.npix, b.cell_rad)
 
-    def total(self) -> int:
+    def total(self, per_px: int = 1) -> int:
+        """Output floats needed: per_px = 2 for complex cutouts (PSF_COMPLEX_OUT), whose
+        packed default offsets advance by 2 N^2."""
         if self.npos == 0:
             return 0
-        return int((self.offsets + self.npix.astype(np.int64) ** 2).max())
+        n2 = self.npix.astype(np.int64) ** 2
+        if self._given is None:
+            return int(per_px * n2.sum())
+        return int((self.offsets + per_px * n2).max())
 
     def struct(self) -> _lib.BatchT:
         return _lib.BatchT(self.npos, self.lm.ctypes.data if self.npos else None,
@@ -92,11 +97,13 @@ class Plan:
         check(_lib.lib().psf_plan_set_opts(self._h, ctypes.byref(opts)), "psf_plan_set_opts")
 
     def forward(self, method: str, batch: Batch, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """Cutouts of `method` ('exact' | 'uv' | 'img') into a device float32 tensor."""
+        """Cutouts of `method` ('exact' | 'uv' | 'img') into a device float32 tensor
+        (with PSF_COMPLEX_OUT: N^2 real parts then N^2 imaginary parts per cutout)."""
+        per = 2 if (self.flags & _lib.PSF_COMPLEX_OUT) else 1
         if out is None:
-            out = torch.empty(max(batch.total(), 1), dtype=torch.float32, device="cuda")
+            out = torch.empty(max(batch.total(per), 1), dtype=torch.float32, device="cuda")
         assert out.dtype == torch.float32 and out.is_cuda and out.is_contiguous()
-        assert out.numel() >= batch.total()
+        assert out.numel() >= batch.total(per)
         fn = {"exact": "psf_exact", "uv": "psf_approx_uv", "img": "psf_approx_img"}[method]
         bs = batch.struct()
         check(getattr(_lib.lib(), fn)(self._h, ctypes.byref(bs), ctypes.c_void_p(out.data_ptr()),
@@ -116,11 +123,12 @@ class Plan:
                       out_img: Optional[torch.Tensor] = None, stream=None):
         """Methods 1 and 2 of one batch in one call: (uv cutouts, image-plane cutouts)."""
         outs = []
+        per = 2 if (self.flags & _lib.PSF_COMPLEX_OUT) else 1
         for o in (out_uv, out_img):
             if o is None:
-                o = torch.empty(max(batch.total(), 1), dtype=torch.float32, device="cuda")
+                o = torch.empty(max(batch.total(per), 1), dtype=torch.float32, device="cuda")
             assert o.dtype == torch.float32 and o.is_cuda and o.is_contiguous()
-            assert o.numel() >= batch.total()
+            assert o.numel() >= batch.total(per)
             outs.append(o)
         bs = batch.struct()
         check(_lib.lib().psf_approx_uv_img(self._h, ctypes.byref(bs), ctypes.c_void_p(outs[0].data_ptr()),

@@ -72,7 +72,10 @@ constexpr int kATileBytes = 128 * 128;
 // tile + R0 * 128 with R0 a multiple of 8; the packed pair's imaginary half is the
 // high 16 bits, so conjugation is a sign-bit XOR), and with `tail` the conjugate of
 // the value one step past the last row at `tail_addr` (row 0 of the tile).
-template <int BF16, bool MIRROR = false>
+// CPLX: each row value z is also written as (-Im z, Re z) at row r of base + mbase
+// (the second half of a doubled B tile: with z = conj(a) these rows give the
+// imaginary part of the contraction).
+template <int BF16, bool MIRROR = false, bool CPLX = false>
 __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float2 wk,
                                             bool weighted, uint32_t mbase = 0, bool tail = false,
                                             uint32_t tail_addr = 0) {
@@ -116,6 +119,11 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
             if (MIRROR)
                 stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)q * 128u + ((ca ^ ((8u - q) & 7u)) << 4),
                             v0 ^ kConj, v1 ^ kConj, v2 ^ kConj, v3 ^ kConj);
+            if (CPLX)
+                stmatrix_x4(base + mbase + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)q * 128u +
+                                (((threadIdx.x & 7u) ^ (uint32_t)q) << 4),
+                            pack2<BF16>(-im[0].x, re[0].x), pack2<BF16>(-im[1].x, re[1].x),
+                            pack2<BF16>(-im[0].y, re[0].y), pack2<BF16>(-im[1].y, re[1].y));
         }
         {
             const uint32_t v4 = pack2<BF16>(re[2].x, im[2].x), v5 = pack2<BF16>(re[3].x, im[3].x);
@@ -127,6 +135,11 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
             if (MIRROR)
                 stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)(q + 4) * 128u + ((ca ^ ((4u - q) & 7u)) << 4),
                             v4 ^ kConj, v5 ^ kConj, v6 ^ kConj, v7 ^ kConj);
+            if (CPLX)
+                stmatrix_x4(base + mbase + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)(q + 4) * 128u +
+                                (((threadIdx.x & 7u) ^ (uint32_t)(q + 4)) << 4),
+                            pack2<BF16>(-im[2].x, re[2].x), pack2<BF16>(-im[3].x, re[3].x),
+                            pack2<BF16>(-im[2].y, re[2].y), pack2<BF16>(-im[3].y, re[3].y));
         }
         if (q < 3) {
 #pragma unroll
@@ -240,7 +253,9 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages, ui
 // the B operand (2 N rows) the row twiddles times the Method 1 weights (rows 0 .. N-1)
 // and times the Method 2 weights (rows N .. 2N-1), so one N = 2 ncols MMA yields both
 // cutouts side by side in TMEM (w2: second weight rows; part2: offset of the second
-// cutout's partial sums from `partial`).
+// cutout's partial sums from `partial`); 5 = complex output: A as in mode 0, B of 2 ncols
+// rows = the conjugated row twiddles (a_r, -a_i) and then (a_i, a_r), so the two halves
+// of the accumulator are the real and the imaginary parts of the cutout.
 template <int BF16, int kStages, int NISS, int MIR>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
@@ -249,7 +264,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the operand tiles (swizzle atoms)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    constexpr int kBMul = (MIR == 4) ? 2 : 1;                       // B rows per output column
+    constexpr int kBMul = (MIR == 4 || MIR == 5) ? 2 : 1;           // B rows per output column
     constexpr uint32_t kSlot = (MIR == 4) ? kKS * 24 : kInSlotBytes;   // uv, w (, w2) per visibility
     const SmemLayout L = smem_layout(kBMul * ncols_max, kStages, kSlot);
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
@@ -306,7 +321,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         // generated; rows 1 .. N/2 are their conjugates and row 0 the conjugate of the
         // value one step past row N-1.
         const bool mirror = (MIR == 2) || (MIR == 4) || (MIR == 1 && it.j0 == 0 && it.i0 == 0 && it.ncols == it.N && it.N <= 128 && (it.N & 63) == 0);
-        const int nA = mirror ? it.N / 64 : 4;            // 32-row chains of the A (128 rows) and B tiles
+        // 32-row chains of the A (128 rows) and B tiles (complex output: A rows past the
+        // cutout are skipped)
+        const int nA = mirror ? it.N / 64 : (MIR == 5 ? min(4, (it.N - it.j0 + 31) / 32) : 4);
         const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
@@ -330,7 +347,14 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kATileBytes);
             const uint32_t b_tile = smem_u32(smem + L.b_off + slot * bt_stride);
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
-                if (MIR == 4) {   // A: unweighted column twiddles; B: weighted row twiddles, both halves
+                if (MIR == 5) {   // A: weighted column twiddles; B: row twiddles, real and imaginary halves
+                    if (ch < nA)
+                        gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk, true);
+                    else
+                        gen_chain32<BF16, false, true>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
+                                                       it.i0 + (ch - nA) * 32 - half, wk, false,
+                                                       (uint32_t)ncols * 128u);
+                } else if (MIR == 4) {   // A: unweighted column twiddles; B: weighted row twiddles, both halves
                     const bool isA = ch < nA;
                     const int c = isA ? ch : ch - nA;
                     const int R0 = half + 32 * c;
@@ -455,7 +479,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (row_ok)
                 for (int c = 0; c < ncol_valid; ++c) {
                     dst[c * cstride] = 0.f;
-                    if (MIR == 4) dst2[c * cstride] = 0.f;
+                    if (kBMul == 2) dst2[c * cstride] = 0.f;
                 }
         }
         const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
@@ -470,8 +494,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t ta = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)b * acc_cols;
             for (int c0 = 0; c0 < kBMul * ncols; c0 += 16) {
                 // fused form: columns ncols .. 2 ncols - 1 are the second cutout
-                float *const dd = (MIR == 4 && c0 >= ncols) ? dst2 : dst;
-                const int cb = (MIR == 4 && c0 >= ncols) ? c0 - ncols : c0;
+                float *const dd = (kBMul == 2 && c0 >= ncols) ? dst2 : dst;
+                const int cb = (kBMul == 2 && c0 >= ncols) ? c0 - ncols : c0;
                 float v[16];
                 tmem_ld16(ta + (uint32_t)c0, v);
                 if (two) {
@@ -609,7 +633,7 @@ template <int BF16, int S, int NISS, int MIR>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                                int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
                                cudaStream_t st, const float2 *w2 = nullptr, int64_t part2 = 0) {
-    const SmemLayout L = smem_layout((MIR == 4 ? 2 : 1) * ncols_max, S, MIR == 4 ? kKS * 24 : kInSlotBytes);
+    const SmemLayout L = smem_layout((MIR == 4 || MIR == 5 ? 2 : 1) * ncols_max, S, MIR == 4 ? kKS * 24 : kInSlotBytes);
     const size_t bytes = L.bytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)bytes);
@@ -656,6 +680,23 @@ cudaError_t launch_psf_tc_uvimg(const DevObs &o, const float2 *w_uv, const float
                                           w_img, part2)
                 : launch_tc_t<0, 4, 1, 4>(o, w_uv, ldw, items, nitems, 128, cell, partial, split_stride, err, st,
                                           w_img, part2);
+}
+
+cudaError_t launch_psf_tc_cplx(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
+                               int ncols_max, int bf16, float cell, float *partial, int64_t split_stride,
+                               int64_t part2, int *err, cudaStream_t st) {
+    if (nitems <= 0) return cudaSuccess;
+    if (ncols_max > 128) return cudaErrorInvalidValue;
+    // B tiles of 2 ncols rows: <= 128 rows -> 6 stages, two issuers; up to 256 -> 4, one
+    if (2 * ncols_max <= 128)
+        return bf16 ? launch_tc_t<1, 6, 2, 5>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err,
+                                              st, nullptr, part2)
+                    : launch_tc_t<0, 6, 2, 5>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err,
+                                              st, nullptr, part2);
+    return bf16 ? launch_tc_t<1, 4, 1, 5>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err, st,
+                                          nullptr, part2)
+                : launch_tc_t<0, 4, 1, 5>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, err, st,
+                                          nullptr, part2);
 }
 
 int selftest_umma(const void *a, const void *b, float *d, int n) {

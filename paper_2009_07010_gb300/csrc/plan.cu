@@ -141,7 +141,7 @@ int validate_obs(const psf_obs_t *o) {
 int validate_opts(const psf_opts_t *op) {
     if (!op) return PSF_OK;
     if (op->prec != PSF_FP32 && op->prec != PSF_TC_FP16 && op->prec != PSF_TC_BF16) return PSF_EINVAL;
-    if (op->flags & ~(PSF_WTERM | PSF_IMG_LITERAL_THETA)) return PSF_EINVAL;
+    if (op->flags & ~(PSF_WTERM | PSF_IMG_LITERAL_THETA | PSF_DETERMINISTIC | PSF_COMPLEX_OUT)) return PSF_EINVAL;
     if (op->algo != PSF_ALGO_AUTO && op->algo != PSF_ALGO_CUTOUT) return PSF_EINVAL;
     return PSF_OK;
 }
@@ -379,7 +379,9 @@ struct BatchHost {
     double cell = 0;
 };
 
-int prepare_batch(const psf_plan_s *p, const psf_batch_t *b, BatchHost &h, int max_n) {
+// per_px: floats per output pixel (2 with complex output: N^2 real parts, then N^2
+// imaginary parts per cutout).
+int prepare_batch(const psf_plan_s *p, const psf_batch_t *b, BatchHost &h, int max_n, int per_px = 1) {
     if (!b || b->npos < 0) return PSF_EINVAL;
     h.npos = b->npos;
     if (b->npos == 0) return PSF_OK;
@@ -404,7 +406,7 @@ int prepare_batch(const psf_plan_s *p, const psf_batch_t *b, BatchHost &h, int m
             h.out_off[i] = b->out_offset[i];
         } else {
             h.out_off[i] = run;
-            run += (int64_t)N * N;
+            run += (int64_t)per_px * N * N;
         }
     }
     if (b->out_offset) {   // cutouts must not overlap
@@ -413,7 +415,7 @@ int prepare_batch(const psf_plan_s *p, const psf_batch_t *b, BatchHost &h, int m
         std::sort(idx.begin(), idx.end(), [&](int a, int c) { return h.out_off[a] < h.out_off[c]; });
         for (int i = 1; i < b->npos; ++i) {
             const int a = idx[i - 1];
-            if (h.out_off[a] + (int64_t)h.npix[a] * h.npix[a] > h.out_off[idx[i]]) return PSF_EINVAL;
+            if (h.out_off[a] + (int64_t)per_px * h.npix[a] * h.npix[a] > h.out_off[idx[i]]) return PSF_EINVAL;
         }
     }
     return PSF_OK;
@@ -549,18 +551,22 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
     return PSF_OK;
 }
 
+int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, cudaStream_t st);
+
 int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st) {
     if (!p || !out) return PSF_EINVAL;
     const bool tc = p->opts.prec != PSF_FP32;
+    const bool cplx = (p->opts.flags & PSF_COMPLEX_OUT) != 0;
     BatchHost hall;
-    int s = prepare_batch(p, b, hall, tc ? 256 : 4096);
+    int s = prepare_batch(p, b, hall, cplx ? 128 : (tc ? 256 : 4096), cplx ? 2 : 1);
     if (s || hall.npos == 0) return s;
+    if (cplx) return tc ? run_forward_cplx(p, method, hall, out, st) : PSF_EUNSUPPORTED;
     const int64_t K = p->nvis;
     // Batched tensor-core form for large groups of one eligible size; the rest goes
     // through the per-cutout form below.
     BatchHost h;
     h.cell = hall.cell;
-    if (tc && p->opts.algo == PSF_ALGO_AUTO) {
+    if (tc && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC)) {
         std::vector<std::vector<int>> groups(257);
         for (int i = 0; i < hall.npos; ++i) {
             const int N = hall.npix[i];
@@ -721,6 +727,10 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
 int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float *out_img, cudaStream_t st) {
     if (!p || !out_uv || !out_img) return PSF_EINVAL;
     const bool tc = p->opts.prec != PSF_FP32;
+    if (p->opts.flags & PSF_COMPLEX_OUT) {   // the fused pass writes real parts only
+        const int s2 = run_forward(p, kUV, b, out_uv, st);
+        return s2 ? s2 : run_forward(p, kImg, b, out_img, st);
+    }
     BatchHost h;
     int s = prepare_batch(p, b, h, tc ? 256 : 4096);
     if (s || h.npos == 0) return s;
@@ -731,7 +741,9 @@ int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float 
         else if (h.npix[i] == 128) ++n128;
         else fused = false;
     }
-    if (fused && p->opts.algo == PSF_ALGO_AUTO && (n64 >= kKrMinGroup || n128 >= kKrMinGroup)) fused = false;
+    if (fused && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC) &&
+        (n64 >= kKrMinGroup || n128 >= kKrMinGroup))
+        fused = false;
     if (!fused) {
         s = run_forward(p, kUV, b, out_uv, st);
         return s ? s : run_forward(p, kImg, b, out_img, st);
@@ -817,6 +829,94 @@ int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float 
         p->n_kernels++;
         PSF_TRY(launch_reduce(part, nsplit, chunk_px, d_loc, d_out, d_npix, cn, 1, out_uv, st));
         PSF_TRY(launch_reduce(part + part2, nsplit, chunk_px, d_loc, d_out, d_npix, cn, 1, out_img, st));
+        p->n_kernels += 2;
+    }
+    return PSF_OK;
+}
+
+// Complex output: one per-cutout item per position (N <= 128, one row tile), B
+// doubled into real and imaginary halves, split partials of both halves reduced in
+// float64 into the cutout's N^2 real parts and the N^2 imaginary parts after them.
+int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, cudaStream_t st) {
+    const int64_t K = p->nvis;
+    const int chunk = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(h.npos, 32768), kWeightBudget / (K * 8)));
+    for (int c0 = 0; c0 < h.npos; c0 += chunk) {
+        const int cn = std::min(chunk, h.npos - c0);
+        std::vector<int64_t> loc(cn), out_im(cn);
+        int64_t chunk_px = 0;
+        int ncols_max = 32;
+        std::vector<TcItem> base, items;
+        for (int i = 0; i < cn; ++i) {
+            const int N = h.npix[c0 + i];
+            loc[i] = chunk_px;
+            chunk_px += (int64_t)N * N;
+            out_im[i] = h.out_off[c0 + i] + (int64_t)N * N;
+            const int nc = (N + 31) / 32 * 32;
+            ncols_max = std::max(ncols_max, nc);
+            base.push_back(TcItem{i, N, 0, 0, nc, 0, 0, 0, loc[i]});
+        }
+        int nsplit = (int)std::max<int64_t>(1, std::min<int64_t>((p->nsm + cn - 1) / cn, (K + 8191) / 8192));
+        const int32_t kper = (int32_t)(((K + nsplit - 1) / nsplit + 31) / 32 * 32);
+        nsplit = (int)((K + kper - 1) / kper);
+        for (int sp = 0; sp < nsplit; ++sp)
+            for (auto it : base) {
+                it.k0 = (int32_t)(sp * (int64_t)kper);
+                it.k1 = (int32_t)std::min<int64_t>(K, (int64_t)(sp + 1) * kper);
+                it.split = sp;
+                items.push_back(it);
+            }
+        // metadata block: pos | npix | loc offs | out offs (real) | out offs (imaginary) | items
+        const size_t off_pos = 0;
+        const size_t off_npix = align_up(off_pos + cn * sizeof(float4), 16);
+        const size_t off_loc = align_up(off_npix + cn * sizeof(int32_t), 16);
+        const size_t off_out = align_up(off_loc + cn * sizeof(int64_t), 16);
+        const size_t off_outi = align_up(off_out + cn * sizeof(int64_t), 16);
+        const size_t off_items = align_up(off_outi + cn * sizeof(int64_t), 16);
+        const size_t bytes = align_up(off_items + items.size() * sizeof(TcItem), 16);
+        std::vector<char> blob(bytes, 0);
+        std::memcpy(blob.data() + off_pos, &h.pos[c0], cn * sizeof(float4));
+        std::memcpy(blob.data() + off_npix, &h.npix[c0], cn * sizeof(int32_t));
+        std::memcpy(blob.data() + off_loc, loc.data(), cn * sizeof(int64_t));
+        std::memcpy(blob.data() + off_out, &h.out_off[c0], cn * sizeof(int64_t));
+        std::memcpy(blob.data() + off_outi, out_im.data(), cn * sizeof(int64_t));
+        std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(TcItem));
+        int s = upload_meta(p, blob.data(), bytes, st);
+        if (s) return s;
+        char *dm = (char *)p->meta.p;
+        const float4 *d_pos = (const float4 *)(dm + off_pos);
+        const int32_t *d_npix = (const int32_t *)(dm + off_npix);
+        const int64_t *d_loc = (const int64_t *)(dm + off_loc);
+        const int64_t ldw = (K + 31) / 32 * 32;
+        PSF_TRY(p->wbuf.reserve((size_t)(cn * ldw + 64) * sizeof(float2)));
+        float2 *w = (float2 *)p->wbuf.p;
+        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, 1, st));
+        p->n_kernels++;
+        const int64_t part2 = (int64_t)nsplit * chunk_px;
+        PSF_TRY(p->partial.reserve((size_t)(2 * part2) * sizeof(float)));
+        float *part = (float *)p->partial.p;
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        if (p->prof) {
+            if (p->prof_used == p->prof_ev.size()) {
+                cudaEvent_t a, c;
+                PSF_TRY(cudaEventCreate(&a));
+                PSF_TRY(cudaEventCreate(&c));
+                p->prof_ev.emplace_back(a, c);
+            }
+            ev1 = p->prof_ev[p->prof_used].first;
+            ev2 = p->prof_ev[p->prof_used].second;
+            p->prof_used++;
+            PSF_TRY(cudaEventRecord(ev1, st));
+        }
+        PSF_TRY(launch_psf_tc_cplx(p->d, w, ldw, (const TcItem *)(dm + off_items), (int)items.size(), ncols_max,
+                                   p->opts.prec == PSF_TC_BF16, (float)h.cell, part, chunk_px, part2,
+                                   (int *)p->err.p, st));
+        if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+        p->n_contract++;
+        p->n_kernels++;
+        PSF_TRY(launch_reduce(part, nsplit, chunk_px, d_loc, (const int64_t *)(dm + off_out), d_npix, cn, 1, out, st));
+        PSF_TRY(launch_reduce(part + part2, nsplit, chunk_px, d_loc, (const int64_t *)(dm + off_outi), d_npix, cn, 1,
+                              out, st));
         p->n_kernels += 2;
     }
     return PSF_OK;

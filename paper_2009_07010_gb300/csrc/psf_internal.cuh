@@ -94,6 +94,11 @@ cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const T
 cudaError_t launch_psf_tc_uvimg(const DevObs &o, const float2 *w_uv, const float2 *w_img, int64_t ldw,
                                 const TcItem *items, int nitems, int ncols_max, int bf16, float cell, float *partial,
                                 int64_t split_stride, int64_t part2, int *err, cudaStream_t st);
+// Complex output (every item: one row tile, ncols <= 128): partial sums of the real
+// parts at `partial`, of the imaginary parts at partial + part2.
+cudaError_t launch_psf_tc_cplx(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
+                               int ncols_max, int bf16, float cell, float *partial, int64_t split_stride,
+                               int64_t part2, int *err, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
 int selftest_timeout(int limit_ms);
 

@@ -107,3 +107,5 @@ def test_header_constants_match_binding():
     assert int(consts["PSF_TC_BF16"]) == _lib.PSF_TC_BF16
     assert int(consts["PSF_WTERM"]) == _lib.PSF_WTERM
     assert int(consts["PSF_IMG_LITERAL_THETA"]) == _lib.PSF_IMG_LITERAL_THETA
+    assert int(consts["PSF_DETERMINISTIC"]) == _lib.PSF_DETERMINISTIC
+    assert int(consts["PSF_COMPLEX_OUT"]) == _lib.PSF_COMPLEX_OUT
