@@ -10,7 +10,10 @@ marshals numpy arrays through ctypes.  ``brute.py`` holds a second, undivided
 evaluation in extended precision used to pin the factored form.
 
 Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
-(closed forms, limits, symmetries, brute force, finite differences).  The
+(closed forms, limits, symmetries, brute force, finite differences) and, for the
+gridded image-plane form, ``tests/test_oracle_grid_pins.py`` (numpy FFT, exact
+agreement with the visibility-level Method 2 on cell-centred uv points, brute-force
+gridding, symmetry).  The
 accuracy levels the paper reads off its MeerKAT figures (Sect. 4, Figs. 4-7)
 are *parity unpinned*: they need the paper's array, dataset and imager.
 """
@@ -34,11 +37,12 @@ WTERM, LITERAL_THETA = 1, 2
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle shared object (gcc, OpenMP, no fast-math)."""
+    """Compile the oracle shared object (gcc, OpenMP, no fast-math, no FMA contraction:
+    the nearest-cell decisions of the gridded form must round as written)."""
     if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
         tmp = _SO + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+                               "-fno-fast-math", "-ffp-contract=off", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _SO)
     return _SO
 
@@ -60,6 +64,11 @@ def _load():
             lib.or_psf.restype = ctypes.c_int
             lib.or_psf.argtypes = obs_args + [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
                                               ctypes.c_int, P, P, ctypes.c_int64, P]
+            lib.or_grid_tables.restype = ctypes.c_int
+            lib.or_grid_tables.argtypes = obs_args + [ctypes.c_int, ctypes.c_double, P, P, P, P, P]
+            lib.or_psf_img_grid.restype = ctypes.c_int
+            lib.or_psf_img_grid.argtypes = obs_args + [ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
+                                                       ctypes.c_int, P]
             lib.or_vjp.restype = ctypes.c_int
             lib.or_vjp.argtypes = obs_args + [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
                                               ctypes.c_int, P, P, P, P]
@@ -159,3 +168,31 @@ def vjp(obs, method: int, batch, R: np.ndarray, flags: int = 0, offsets=None):
     if rc != 0:
         raise ValueError("invalid observation")
     return g_lm, g_W
+
+
+def grid_tables(obs, npix: int, cell: float) -> dict:
+    """Position-independent tables of the gridded image-plane form (Eq. 45, Algorithm 1)
+    on the npix x npix uv grid of the cutout: S = F{P} (complex [b, a]), per-cell mean
+    dt and dnu/nu, per-cell weight sum, and the effective PSF P [j, i]."""
+    o = _Obs(obs)
+    N = int(npix)
+    S = np.empty((N, N, 2))
+    dt = np.empty((N, N))
+    r = np.empty((N, N))
+    ws = np.empty((N, N))
+    P = np.empty((N, N))
+    if _load().or_grid_tables(*o.args(), N, float(cell), _p(S), _p(dt), _p(r), _p(ws), _p(P)) != 0:
+        raise ValueError("invalid observation or grid")
+    return dict(S=S[..., 0] + 1j * S[..., 1], dt=dt, r=r, wsum=ws, P=P)
+
+
+def psf_img_grid(obs, lm, npix: int, cell: float, flags: int = 0) -> np.ndarray:
+    """Gridded image-plane cutouts [npos, npix, npix] (float64): Re F^-1{F{P} D} with D of
+    Algorithm 1 at each uv cell."""
+    o = _Obs(obs)
+    lm = np.ascontiguousarray(np.asarray(lm, np.float64).reshape(-1, 2))
+    N = int(npix)
+    out = np.empty((lm.shape[0], N, N))
+    if _load().or_psf_img_grid(*o.args(), lm.shape[0], _p(lm), N, float(cell), int(flags), _p(out)) != 0:
+        raise ValueError("invalid observation or grid")
+    return out

@@ -15,6 +15,7 @@
  *     visibilities ................................... Eqs. 21-23
  *   - Method 1 (uv-plane) sinc x sinc decorrelation ... Eqs. 31-35
  *   - Method 2 (image-plane) circular-track model ..... Eqs. 38-44, Algorithm 1
+ *   - Method 2 gridded on the cutout's uv grid ........ Eq. 45, Algorithm 1
  *   - vector-Jacobian product of the PSF sum (adjoint)  chain rule on Eqs. 21-22
  *
  * Conventions (readings of the paper, one line each):
@@ -157,6 +158,34 @@ static void or_direction(double l0, double m0, int flags, double L[3], double dL
 
 static double or_dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
+/* Method 2 (Eqs. 38-44, Algorithm 1) at one uv point (u, v) [lambda] with time interval
+ * dt and fractional bandwidth r = dnu / nu: D = sinc(dPsi/2) sinc(dPhi/2) and its
+ * derivatives with respect to l0 and m0.  w is ignored. */
+static void or_img_decorr(double u, double v, double dt, double r, double l0, double m0, int flags,
+                          double *D, double *Dl, double *Dm) {
+    double uvlen = sqrt(u * u + v * v);
+    double udot, vdot;   /* Eqs. 40-41 divided by omega_E */
+    if (flags & OR_LITERAL_THETA) {
+        double th = (v != 0.0) ? atan(u / v) : (u >= 0 ? OR_PI / 2 : -OR_PI / 2);
+        udot = -uvlen * sin(th);
+        vdot = uvlen * cos(th);
+    } else {
+        double th = atan2(v, u);
+        udot = -uvlen * sin(th);
+        vdot = uvlen * cos(th);
+    }
+    double rho = sqrt(l0 * l0 + m0 * m0);
+    double A = OR_OMEGA_E * dt * (udot * l0 + vdot * m0);        /* dPsi / (2 pi) */
+    double B = r * uvlen * rho;                                 /* dPhi / (2 pi) */
+    double Al = OR_OMEGA_E * dt * udot, Am = OR_OMEGA_E * dt * vdot;
+    double Bl = rho > 0 ? r * uvlen * l0 / rho : 0.0;
+    double Bm = rho > 0 ? r * uvlen * m0 / rho : 0.0;
+    double sA = or_sincpi(A), sB = or_sincpi(B), dA = or_dsincpi(A), dB = or_dsincpi(B);
+    *D = sA * sB;
+    *Dl = dA * Al * sB + sA * dB * Bl;
+    *Dm = dA * Am * sB + sA * dB * Bm;
+}
+
 /* Decorrelation D_k(l0) and its gradient, for one averaged visibility.
  *   exact (method 0): Eq. 13 with the centre-visibility phase removed, i.e.
  *     D = (1/n) sum_s sum_c (dnu_c / Dnu_r) exp(-2 pi i (nu_c X_s - nu_r Xbar) / c)
@@ -205,27 +234,7 @@ static void or_decorr_one(const or_obs *o, const or_vis *x, int method, double l
         gm_re = dA * Am * sB + sA * dB * Bm;
     } else {
         double u = x->ubar[0] * x->nu / OR_C_LIGHT, v = x->ubar[1] * x->nu / OR_C_LIGHT;
-        double uvlen = sqrt(u * u + v * v);
-        double udot, vdot;   /* Eqs. 40-41 divided by omega_E */
-        if (flags & OR_LITERAL_THETA) {
-            double th = (v != 0.0) ? atan(u / v) : (u >= 0 ? OR_PI / 2 : -OR_PI / 2);
-            udot = -uvlen * sin(th);
-            vdot = uvlen * cos(th);
-        } else {
-            double th = atan2(v, u);
-            udot = -uvlen * sin(th);
-            vdot = uvlen * cos(th);
-        }
-        double rho = sqrt(l0 * l0 + m0 * m0);
-        double A = OR_OMEGA_E * x->dt * (udot * l0 + vdot * m0);        /* dPsi / (2 pi) */
-        double B = (x->dnu / x->nu) * uvlen * rho;                      /* dPhi / (2 pi) */
-        double Al = OR_OMEGA_E * x->dt * udot, Am = OR_OMEGA_E * x->dt * vdot;
-        double Bl = rho > 0 ? (x->dnu / x->nu) * uvlen * l0 / rho : 0.0;
-        double Bm = rho > 0 ? (x->dnu / x->nu) * uvlen * m0 / rho : 0.0;
-        double sA = or_sincpi(A), sB = or_sincpi(B), dA = or_dsincpi(A), dB = or_dsincpi(B);
-        re = sA * sB;
-        gl_re = dA * Al * sB + sA * dB * Bl;
-        gm_re = dA * Am * sB + sA * dB * Bm;
+        or_img_decorr(u, v, x->dt, x->dnu / x->nu, l0, m0, flags, &re, &gl_re, &gm_re);
     }
     *Dre = re; *Dim = im;
     if (g) { g[0] = gl_re; g[1] = gl_im; g[2] = gm_re; g[3] = gm_im; }
@@ -371,4 +380,160 @@ int or_vjp(OR_OBS_ARGS, int method, int npos, const double *lm, const int *npix,
     }
     free(v);
     return 0;
+}
+
+/* ---------------------------------------------------------------------------------
+ * Gridded image-plane approximation: Eq. 45 with Algorithm 1 evaluated on uv cells.
+ *
+ * Readings (the paper leaves these open):
+ *   - the grid is the N x N Fourier grid of the N x N cutout: cell spacing
+ *     du = dv = 1 / (N cell), cell (a, b) at u = (a - N/2) du, v = (b - N/2) dv, so that
+ *     the pixel phase 2 pi u dl is 2 pi (a - N/2)(i - N/2) / N and the transform pair is
+ *     the N x N DFT; the cell steps of Algorithm 1 are read as exactly du, dv, and its
+ *     half-cell start offset as this DFT-conjugate origin
+ *   - F{P} is the DFT of the effective PSF P, the cutout at the phase centre with no
+ *     distortion: P[j][i] = sum_k W_k cos(2 pi (u_k dl_i + v_k dm_j))
+ *   - Algorithm 1 holds one dt, dnu and nu; with several channels and baseline-dependent
+ *     averaging each cell takes the W-weighted means of dt_k and dnu_r / nu_r over the
+ *     visibilities nearest to it and over the conjugates of those nearest to its mirror
+ *     cell (a visibility at c also samples -c), cells taken modulo N (the DFT cannot tell
+ *     u from u + N du); cells that receive none take the means over all visibilities
+ *   - nearest cell: a' = floor(u_k N cell + 0.5) with u_k = ubar nu_r / c, evaluated in
+ *     double precision in that order (the library decides the same way)
+ *   - the cutout is Re F^-1{F{P} D}, F^-1 with the 1/N^2 of the inverse DFT
+ * --------------------------------------------------------------------------------- */
+
+/* Twiddle table tw[x][y] = exp(+2 pi i (x - N/2)(y - N/2) / N), angle reduced exactly. */
+static void or_grid_twiddles(int N, double *twr, double *twi) {
+    for (int x = 0; x < N; ++x)
+        for (int y = 0; y < N; ++y) {
+            int64_t m = ((int64_t)(x - N / 2) * (int64_t)(y - N / 2)) % N;
+            if (m < 0) m += N;
+            twr[x * N + y] = cos(2 * OR_PI * (double)m / N);
+            twi[x * N + y] = sin(2 * OR_PI * (double)m / N);
+        }
+}
+
+static int or_mod(int64_t x, int N) {
+    int64_t r = x % N;
+    return (int)(r < 0 ? r + N : r);
+}
+
+/* Position-independent tables of the gridded form:
+ *   S    [N][N][2] F{P} (row b = v cell, column a = u cell; re, im)
+ *   dtc  [N][N]    per-cell mean dt, rc [N][N] per-cell mean dnu/nu
+ *   wsum [N][N]    per-cell sum of W over the visibilities and conjugates it received
+ *   P    [N][N]    the effective PSF (any of the outputs may be NULL). */
+int or_grid_tables(OR_OBS_ARGS, int N, double cell, double *S, double *dtc, double *rc, double *wsum,
+                   double *Pout) {
+    or_obs o = OR_OBS_INIT;
+    int64_t nvis;
+    if (N < 2 || N % 2 || !(cell > 0)) return -1;
+    or_vis *v = or_make_vis(&o, &nvis);
+    if (!v) return -1;
+    const int64_t NN = (int64_t)N * N;
+    double *P = (double *)calloc((size_t)NN, sizeof(double));
+    double *twr = (double *)malloc(sizeof(double) * NN), *twi = (double *)malloc(sizeof(double) * NN);
+    double *sw = (double *)calloc((size_t)NN, sizeof(double));
+    double *sdt = (double *)calloc((size_t)NN, sizeof(double));
+    double *sr = (double *)calloc((size_t)NN, sizeof(double));
+    or_grid_twiddles(N, twr, twi);
+
+    /* effective PSF (Eqs. 21-22 with D = 1) */
+    #pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < NN; ++q) {
+        int i = (int)(q % N), j = (int)(q / N);
+        double dl = (i - N / 2) * cell, dm = (j - N / 2) * cell, acc = 0;
+        for (int64_t k = 0; k < nvis; ++k) {
+            double u = v[k].ubar[0] * v[k].nu / OR_C_LIGHT, w = v[k].ubar[1] * v[k].nu / OR_C_LIGHT;
+            acc += v[k].W * cos(2 * OR_PI * (u * dl + w * dm));
+        }
+        P[q] = acc;
+    }
+
+    /* F{P}: S[b][a] = sum_j sum_i P[j][i] exp(-2 pi i ((a-N/2)(i-N/2) + (b-N/2)(j-N/2)) / N) */
+    if (S) {
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < NN; ++q) {
+            int a = (int)(q % N), b = (int)(q / N);
+            double re = 0, im = 0;
+            for (int j = 0; j < N; ++j)
+                for (int i = 0; i < N; ++i) {
+                    /* exp(-i x) exp(-i y) = conj(tw[a][i] tw[b][j]) */
+                    double cr = twr[a * N + i] * twr[b * N + j] - twi[a * N + i] * twi[b * N + j];
+                    double ci = twr[a * N + i] * twi[b * N + j] + twi[a * N + i] * twr[b * N + j];
+                    re += P[(int64_t)j * N + i] * cr;
+                    im -= P[(int64_t)j * N + i] * ci;
+                }
+            S[2 * q] = re;
+            S[2 * q + 1] = im;
+        }
+    }
+
+    /* per-cell means of dt and dnu/nu, nearest cell and its mirror, modulo N */
+    double gw = 0, gdt = 0, gr = 0;
+    const double s = (double)N * cell;
+    for (int64_t k = 0; k < nvis; ++k) {
+        double u = v[k].ubar[0] * v[k].nu / OR_C_LIGHT, w = v[k].ubar[1] * v[k].nu / OR_C_LIGHT;
+        double qa = u * s, qb = w * s;
+        int64_t ia = (int64_t)floor(qa + 0.5), ib = (int64_t)floor(qb + 0.5);
+        double r = v[k].dnu / v[k].nu, W = v[k].W;
+        int c1 = or_mod(ib + N / 2, N) * N + or_mod(ia + N / 2, N);
+        int c2 = or_mod(-ib + N / 2, N) * N + or_mod(-ia + N / 2, N);
+        sw[c1] += W; sdt[c1] += W * v[k].dt; sr[c1] += W * r;
+        sw[c2] += W; sdt[c2] += W * v[k].dt; sr[c2] += W * r;
+        gw += W; gdt += W * v[k].dt; gr += W * r;
+    }
+    for (int64_t q = 0; q < NN; ++q) {
+        if (dtc) dtc[q] = sw[q] > 0 ? sdt[q] / sw[q] : (gw > 0 ? gdt / gw : 0.0);
+        if (rc) rc[q] = sw[q] > 0 ? sr[q] / sw[q] : (gw > 0 ? gr / gw : 0.0);
+        if (wsum) wsum[q] = sw[q];
+        if (Pout) Pout[q] = P[q];
+    }
+    free(P); free(twr); free(twi); free(sw); free(sdt); free(sr); free(v);
+    return 0;
+}
+
+/* Gridded cutouts: out[p][j N + i] = (1/N^2) Re sum_b sum_a S[b][a] D_ab(l0_p)
+ *                                      exp(2 pi i ((a-N/2)(i-N/2) + (b-N/2)(j-N/2)) / N),
+ * D_ab = Algorithm 1 at the cell centre with the cell's mean dt and dnu/nu. */
+int or_psf_img_grid(OR_OBS_ARGS, int npos, const double *lm, int N, double cell, int flags, double *out) {
+    if (N < 2 || N % 2 || !(cell > 0)) return -1;
+    const int64_t NN = (int64_t)N * N;
+    double *S = (double *)malloc(sizeof(double) * 2 * NN);
+    double *dtc = (double *)malloc(sizeof(double) * NN), *rc = (double *)malloc(sizeof(double) * NN);
+    double *twr = (double *)malloc(sizeof(double) * NN), *twi = (double *)malloc(sizeof(double) * NN);
+    double *Tr = (double *)malloc(sizeof(double) * NN), *Ti = (double *)malloc(sizeof(double) * NN);
+    int rc0 = or_grid_tables(nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights, N, cell,
+                             S, dtc, rc, NULL, NULL);
+    if (rc0 == 0) {
+        or_grid_twiddles(N, twr, twi);
+        const double du = 1.0 / ((double)N * cell);
+        for (int p = 0; p < npos; ++p) {
+            double l0 = lm[2 * p], m0 = lm[2 * p + 1];
+            for (int64_t q = 0; q < NN; ++q) {
+                int a = (int)(q % N), b = (int)(q / N);
+                double D, Dl, Dm;
+                or_img_decorr((a - N / 2) * du, (b - N / 2) * du, dtc[q], rc[q], l0, m0, flags & OR_LITERAL_THETA,
+                              &D, &Dl, &Dm);
+                Tr[q] = S[2 * q] * D;
+                Ti[q] = S[2 * q + 1] * D;
+            }
+            double *op = out + (int64_t)p * NN;
+            #pragma omp parallel for schedule(dynamic, 1)
+            for (int64_t q = 0; q < NN; ++q) {
+                int i = (int)(q % N), j = (int)(q / N);
+                double acc = 0;
+                for (int b = 0; b < N; ++b)
+                    for (int a = 0; a < N; ++a) {
+                        double cr = twr[a * N + i] * twr[b * N + j] - twi[a * N + i] * twi[b * N + j];
+                        double ci = twr[a * N + i] * twi[b * N + j] + twi[a * N + i] * twr[b * N + j];
+                        acc += Tr[(int64_t)b * N + a] * cr - Ti[(int64_t)b * N + a] * ci;
+                    }
+                op[q] = acc / (double)NN;
+            }
+        }
+    }
+    free(S); free(dtc); free(rc); free(twr); free(twi); free(Tr); free(Ti);
+    return rc0;
 }
