@@ -171,6 +171,30 @@ int psf_approx_img(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, vo
 int psf_approx_uv_img(psf_plan_t plan, const psf_batch_t *batch, float *out_uv_dev, float *out_img_dev,
                       void *cuda_stream);
 
+/* Method 2 in the gridded form of Eq. 45, F^-1{F{P} D} with D of Algorithm 1 evaluated
+ * on uv cells; same arguments and output layout as psf_approx_img.  The grid of an
+ * N x N cutout of pixel size cell is its N x N Fourier grid: cells du = dv = 1/(N cell),
+ * cell (a, b) at ((a - N/2) du, (b - N/2) dv).  Position independent and built on the
+ * first call for each (N, cell_rad, precision), then kept by the plan (that first call
+ * synchronizes the stream): the effective PSF P (the cutout at the phase centre,
+ * evaluated like psf_approx_img in the plan's precision), S = F{P}, and per cell the
+ * W-weighted means of dt_k and Dnu_r / nu_r of the visibilities whose nearest cell,
+ * modulo N, is the cell or its mirror (the means over all visibilities where none is).
+ * Per position: D on every cell (the literal theta with PSF_IMG_LITERAL_THETA), one
+ * inverse N x N FFT, FP32.  It differs from psf_approx_img by the gridding: D is taken at
+ * cell centres and visibilities beyond the grid (|u| > 1/(2 cell)) alias.
+ * N must be 16, 32, 64 or 128 (PSF_EUNSUPPORTED otherwise, and with PSF_COMPLEX_OUT);
+ * PSF_WTERM has no effect (Method 2 ignores w).  Other errors as psf_exact. */
+int psf_approx_img_grid(psf_plan_t plan, const psf_batch_t *batch, float *out_dev, void *cuda_stream);
+
+/* Diagnostic: the position-independent table psf_approx_img_grid uses for (npix,
+ * cell_rad) in the plan's precision (built if needed), copied to table_dev (device
+ * float32 [npix][npix][4]).  Entry [a][b] belongs to the cell at ((a - N/2) du,
+ * (b - N/2) du), du = 1/(N cell_rad): (Re S, Im S) with S = F{P} / N^2, then
+ * omega_E dt_c du and (Dnu/nu)_c |u_c| (dt_c, (Dnu/nu)_c the cell's mean interval and
+ * fractional bandwidth).  Errors as psf_approx_img_grid. */
+int psf_img_grid_table(psf_plan_t plan, int npix, double cell_rad, float *table_dev, void *cuda_stream);
+
 /* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
  * adjoint: given dL/dP (device float32, same layout as the forward output) it
  * writes dL/d(l0,m0) to dL_dlm_dev (device float64 [npos][2], overwritten) and,

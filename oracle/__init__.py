@@ -170,20 +170,24 @@ def vjp(obs, method: int, batch, R: np.ndarray, flags: int = 0, offsets=None):
     return g_lm, g_W
 
 
-def grid_tables(obs, npix: int, cell: float) -> dict:
+def grid_tables(obs, npix: int, cell: float, cells_only: bool = False) -> dict:
     """Position-independent tables of the gridded image-plane form (Eq. 45, Algorithm 1)
     on the npix x npix uv grid of the cutout: S = F{P} (complex [b, a]), per-cell mean
-    dt and dnu/nu, per-cell weight sum, and the effective PSF P [j, i]."""
+    dt and dnu/nu, per-cell weight sum, and the effective PSF P [j, i].  With
+    cells_only, only the per-cell tables (no effective PSF, O(nvis))."""
     o = _Obs(obs)
     N = int(npix)
-    S = np.empty((N, N, 2))
+    S = None if cells_only else np.empty((N, N, 2))
     dt = np.empty((N, N))
     r = np.empty((N, N))
     ws = np.empty((N, N))
-    P = np.empty((N, N))
+    P = None if cells_only else np.empty((N, N))
     if _load().or_grid_tables(*o.args(), N, float(cell), _p(S), _p(dt), _p(r), _p(ws), _p(P)) != 0:
         raise ValueError("invalid observation or grid")
-    return dict(S=S[..., 0] + 1j * S[..., 1], dt=dt, r=r, wsum=ws, P=P)
+    out = dict(dt=dt, r=r, wsum=ws)
+    if not cells_only:
+        out.update(S=S[..., 0] + 1j * S[..., 1], P=P)
+    return out
 
 
 def psf_img_grid(obs, lm, npix: int, cell: float, flags: int = 0) -> np.ndarray:

@@ -439,9 +439,9 @@ int or_grid_tables(OR_OBS_ARGS, int N, double cell, double *S, double *dtc, doub
     double *sr = (double *)calloc((size_t)NN, sizeof(double));
     or_grid_twiddles(N, twr, twi);
 
-    /* effective PSF (Eqs. 21-22 with D = 1) */
+    /* effective PSF (Eqs. 21-22 with D = 1), when S or P is asked for */
     #pragma omp parallel for schedule(dynamic, 1)
-    for (int64_t q = 0; q < NN; ++q) {
+    for (int64_t q = 0; q < ((S || Pout) ? NN : 0); ++q) {
         int i = (int)(q % N), j = (int)(q / N);
         double dl = (i - N / 2) * cell, dm = (j - N / 2) * cell, acc = 0;
         for (int64_t k = 0; k < nvis; ++k) {

@@ -19,7 +19,7 @@ EXACT, UV, IMG = 0, 1, 2
 
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
-           "psf_approx_uv_img", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
+           "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
            "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
 
 
@@ -72,10 +72,12 @@ def lib(auto_build: bool = False):
             L.psf_plan_set_opts.restype = I
             L.psf_plan_nvis.argtypes = [P]
             L.psf_plan_nvis.restype = ctypes.c_int64
-            for name in ("psf_exact", "psf_approx_uv", "psf_approx_img"):
+            for name in ("psf_exact", "psf_approx_uv", "psf_approx_img", "psf_approx_img_grid"):
                 f = getattr(L, name)
                 f.argtypes = [P, ctypes.POINTER(BatchT), P, P]
                 f.restype = I
+            L.psf_img_grid_table.argtypes = [P, I, ctypes.c_double, P, P]
+            L.psf_img_grid_table.restype = I
             L.psf_approx_uv_img.argtypes = [P, ctypes.POINTER(BatchT), P, P, P]
             L.psf_approx_uv_img.restype = I
             L.psf_adjoint.argtypes = [P, I, ctypes.POINTER(BatchT), P, P, P, P]

@@ -97,14 +97,15 @@ class Plan:
         check(_lib.lib().psf_plan_set_opts(self._h, ctypes.byref(opts)), "psf_plan_set_opts")
 
     def forward(self, method: str, batch: Batch, out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
-        """Cutouts of `method` ('exact' | 'uv' | 'img') into a device float32 tensor
+        """Cutouts of `method` ('exact' | 'uv' | 'img' | 'img_grid') into a device float32 tensor
         (with PSF_COMPLEX_OUT: N^2 real parts then N^2 imaginary parts per cutout)."""
         per = 2 if (self.flags & _lib.PSF_COMPLEX_OUT) else 1
         if out is None:
             out = torch.empty(max(batch.total(per), 1), dtype=torch.float32, device="cuda")
         assert out.dtype == torch.float32 and out.is_cuda and out.is_contiguous()
         assert out.numel() >= batch.total(per)
-        fn = {"exact": "psf_exact", "uv": "psf_approx_uv", "img": "psf_approx_img"}[method]
+        fn = {"exact": "psf_exact", "uv": "psf_approx_uv", "img": "psf_approx_img",
+              "img_grid": "psf_approx_img_grid"}[method]
         bs = batch.struct()
         check(getattr(_lib.lib(), fn)(self._h, ctypes.byref(bs), ctypes.c_void_p(out.data_ptr()),
                                       _stream_handle(stream)), fn)
@@ -118,6 +119,18 @@ class Plan:
 
     def approx_img(self, batch, out=None, stream=None):
         return self.forward("img", batch, out, stream)
+
+    def approx_img_grid(self, batch, out=None, stream=None):
+        """Method 2 in the gridded form of Eq. 45 (N in {16, 32, 64, 128})."""
+        return self.forward("img_grid", batch, out, stream)
+
+    def img_grid_table(self, npix: int, cell: float, stream=None) -> torch.Tensor:
+        """Diagnostic: the gridded form's table [npix(a), npix(b), 4] (Re S, Im S,
+        omega_E dt_c du, (dnu/nu)_c |u_c|)."""
+        t = torch.empty((npix, npix, 4), dtype=torch.float32, device="cuda")
+        check(_lib.lib().psf_img_grid_table(self._h, int(npix), float(cell), ctypes.c_void_p(t.data_ptr()),
+                                            _stream_handle(stream)), "psf_img_grid_table")
+        return t
 
     def approx_uv_img(self, batch: Batch, out_uv: Optional[torch.Tensor] = None,
                       out_img: Optional[torch.Tensor] = None, stream=None):

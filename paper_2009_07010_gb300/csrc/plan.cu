@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <memory>
 #include <new>
 #include <thread>
 #include <vector>
@@ -96,6 +97,19 @@ struct psf_plan_s {
     DevObs d{};
     // position-independent device arrays
     DevBuf bin_ubar, bin_edge, bin_samp, samp, chan, rawchan, W, uv;
+    // float64 bin-mean (u, v) [m], output channels (nu_r, Dnu_r) and each baseline's
+    // first bin: the nearest-cell decisions of the gridded image-plane form
+    DevBuf bin_uv64, chan64, bin_first;
+    double dt_raw = 0;
+    // gridded image-plane tables, one per (cutout size, pixel size, precision)
+    struct Grid {
+        int N = 0;
+        double cell = 0;
+        int prec = 0;
+        DevBuf G;   // float4 [N][N]
+    };
+    std::vector<std::unique_ptr<Grid>> grids;
+    DevBuf gpairs;   // per-call pair records of the gridded form
     DevBuf err;          // int: device-side wait timeouts
     // per-call workspace
     DevBuf meta;         // positions, sizes, offsets, tiles
@@ -213,9 +227,12 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     const double dt = o->ntime >= 2 ? (o->time_s[o->ntime - 1] - o->time_s[0]) / (o->ntime - 1) : 0.0;
     std::vector<float4> h_ubar, h_edge, h_samp, h_chan, h_raw;
     std::vector<int2> h_bs;
+    std::vector<double2> h_uv64, h_chan64;
+    std::vector<int32_t> h_bf;
     try {
         h_ubar.resize(nbin); h_edge.resize(nbin); h_bs.resize(nbin); h_samp.resize(nsamp);
         h_chan.resize(nout); h_raw.resize((size_t)o->nchan);
+        h_uv64.resize(nbin); h_chan64.resize(nout); h_bf.resize(o->nbl + 1);
     } catch (...) {
         return fail(PSF_ENOMEM);
     }
@@ -239,6 +256,7 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
             const int64_t bin = bin_first[b] + tau;
             const int64_t rec = samp_first[b] + tau * n;
             h_ubar[bin] = make_float4((float)mean[0], (float)mean[1], (float)mean[2], (float)(n * dt));
+            h_uv64[bin] = make_double2(mean[0], mean[1]);
             h_edge[bin] = make_float4((float)edge[0], (float)edge[1], (float)edge[2], 0.f);
             h_bs[bin] = make_int2((int)rec, n);
             for (int64_t s = 0; s < n; ++s) {
@@ -264,6 +282,7 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
                                    (float)(o->chan_width_hz[c] / dnu), 0.f);
         }
         h_chan[r] = make_float4((float)nu, (float)dnu, (float)sp, (float)wd);
+        h_chan64[r] = make_double2(nu, dnu);
     }
 
     // ---- device copies
@@ -278,7 +297,12 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     UP(samp, h_samp)
     UP(chan, h_chan)
     UP(rawchan, h_raw)
+    for (int b = 0; b <= o->nbl; ++b) h_bf[b] = (int32_t)bin_first[b];
+    UP(bin_uv64, h_uv64)
+    UP(chan64, h_chan64)
+    UP(bin_first, h_bf)
 #undef UP
+    p->dt_raw = dt;
     if (e == cudaSuccess) e = p->W.reserve(nvis * sizeof(float));
     // uv is padded with zeros to a whole number of 32-visibility stages plus one
     // stage, so bulk copies of full stages never leave the buffer
@@ -922,9 +946,137 @@ int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, 
     return PSF_OK;
 }
 
+// Tables of the gridded image-plane form (Eq. 45, Algorithm 1) for one (N, cell,
+// precision), built on first use and kept by the plan: the effective PSF through the
+// visibility-level path (Method 2 at the phase centre, where every decorrelation is 1),
+// its FP64 DFT, the per-cell mean intervals and fractional bandwidths, and the table.
+// The build synchronizes the stream (its temporaries are released on return).
+int grid_tables(psf_plan_s *p, int N, double cell, cudaStream_t st, const float4 **G) {
+    for (auto &g : p->grids)
+        if (g->N == N && g->cell == cell && g->prec == p->opts.prec) {
+            *G = (const float4 *)g->G.p;
+            return PSF_OK;
+        }
+    std::unique_ptr<psf_plan_s::Grid> g(new (std::nothrow) psf_plan_s::Grid());
+    if (!g) return PSF_ENOMEM;
+    g->N = N;
+    g->cell = cell;
+    g->prec = p->opts.prec;
+    const int64_t NN = (int64_t)N * N;
+    DevBuf P, Y, S, acc;
+    PSF_TRY(P.reserve(NN * sizeof(float)));
+    PSF_TRY(Y.reserve(NN * sizeof(double2)));
+    PSF_TRY(S.reserve(NN * sizeof(double2)));
+    PSF_TRY(acc.reserve((3 * NN + 3) * sizeof(double)));
+    PSF_TRY(g->G.reserve(NN * sizeof(float4)));
+    const double lm0[2] = {0.0, 0.0};
+    psf_batch_t b0{};
+    b0.npos = 1;
+    b0.lm = lm0;
+    b0.npix0 = N;
+    b0.cell_rad = cell;
+    int s = run_forward(p, kImg, &b0, (float *)P.p, st);
+    if (s) return s;
+    double *accp = (double *)acc.p;
+    PSF_TRY(launch_grid_dft((const float *)P.p, (double2 *)Y.p, (double2 *)S.p, N, st));
+    PSF_TRY(cudaMemsetAsync(accp, 0, (3 * NN + 3) * sizeof(double), st));
+    PSF_TRY(launch_grid_cells((const double2 *)p->bin_uv64.p, (const int2 *)p->bin_samp.p,
+                              (const int32_t *)p->bin_first.p, (const double2 *)p->chan64.p, p->d.W, p->nbl, p->nout,
+                              p->dt_raw, N, (double)N * cell, accp, accp + 3 * NN, st));
+    PSF_TRY(launch_grid_table((const double2 *)S.p, accp, accp + 3 * NN, N, 1.0 / ((double)N * cell),
+                              (float4 *)g->G.p, st));
+    if (p->prof) p->n_kernels += 4;
+    PSF_TRY(cudaStreamSynchronize(st));
+    *G = (const float4 *)g->G.p;
+    p->grids.push_back(std::move(g));
+    return PSF_OK;
+}
+
+int run_img_grid(psf_plan_s *p, const psf_batch_t *b, float *out, cudaStream_t st) {
+    if (p->opts.flags & PSF_COMPLEX_OUT) return PSF_EUNSUPPORTED;
+    BatchHost h;
+    int s = prepare_batch(p, b, h, 4096);
+    if (s) return s;
+    if (h.npos == 0) return PSF_OK;
+    for (int i = 0; i < h.npos; ++i)
+        if (!img_grid_supported(h.npix[i])) return PSF_EUNSUPPORTED;
+    const bool literal = (p->opts.flags & PSF_IMG_LITERAL_THETA) != 0;
+    // Algorithm 1's A = alpha (c.x a' + c.y b'): (m0, -l0) with theta = atan2(v, u), (-l0, m0)
+    // with the literal arctan(u/v) (the sign of A does not matter to the sinc)
+    auto coef = [&](int i) {
+        const double l0 = b->lm[2 * i], m0 = b->lm[2 * i + 1];
+        const float rho = (float)std::sqrt(l0 * l0 + m0 * m0);
+        return literal ? make_float4((float)-l0, (float)m0, rho, 0.f) : make_float4((float)m0, (float)-l0, rho, 0.f);
+    };
+    static const int kSizes[] = {16, 32, 64, 128};
+    std::vector<GridPair> pairs;
+    int start[4] = {0, 0, 0, 0}, count[4] = {0, 0, 0, 0};
+    const float4 *G[4] = {nullptr, nullptr, nullptr, nullptr};
+    for (int t = 0; t < 4; ++t) {
+        std::vector<int> idx;
+        for (int i = 0; i < h.npos; ++i)
+            if (h.npix[i] == kSizes[t]) idx.push_back(i);
+        if (idx.empty()) continue;
+        if ((s = grid_tables(p, kSizes[t], h.cell, st, &G[t]))) return s;
+        start[t] = (int)pairs.size();
+        for (size_t k = 0; k < idx.size(); k += 2) {
+            GridPair gp{};
+            gp.c0 = coef(idx[k]);
+            gp.off0 = h.out_off[idx[k]];
+            if (k + 1 < idx.size()) {
+                gp.c1 = coef(idx[k + 1]);
+                gp.off1 = h.out_off[idx[k + 1]];
+            } else {
+                gp.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
+                gp.off1 = -1;
+            }
+            pairs.push_back(gp);
+        }
+        count[t] = (int)pairs.size() - start[t];
+    }
+    if ((s = upload_meta(p, pairs.data(), pairs.size() * sizeof(GridPair), st))) return s;
+    for (int t = 0; t < 4; ++t) {
+        if (!count[t]) continue;
+        cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+        if (p->prof) {
+            if (p->prof_used == p->prof_ev.size()) {
+                cudaEvent_t a, e2;
+                PSF_TRY(cudaEventCreate(&a));
+                PSF_TRY(cudaEventCreate(&e2));
+                p->prof_ev.emplace_back(a, e2);
+            }
+            ev1 = p->prof_ev[p->prof_used].first;
+            ev2 = p->prof_ev[p->prof_used].second;
+            p->prof_used++;
+            PSF_TRY(cudaEventRecord(ev1, st));
+        }
+        PSF_TRY(launch_img_grid(G[t], (const GridPair *)p->meta.p + start[t], count[t], kSizes[t], out, p->nsm, st));
+        if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+        p->n_contract++;
+        p->n_kernels++;
+    }
+    return PSF_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int psf_approx_img_grid(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
+    if (!p || !out) return PSF_EINVAL;
+    return run_img_grid(p, b, out, (cudaStream_t)stream);
+}
+
+int psf_img_grid_table(psf_plan_t p, int npix, double cell_rad, float *table_dev, void *stream) {
+    if (!p || !table_dev || !(cell_rad > 0.0)) return PSF_EINVAL;
+    if (!img_grid_supported(npix)) return PSF_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    const float4 *G = nullptr;
+    int s = grid_tables(p, npix, cell_rad, st, &G);
+    if (s) return s;
+    PSF_TRY(cudaMemcpyAsync(table_dev, G, (size_t)npix * npix * sizeof(float4), cudaMemcpyDeviceToDevice, st));
+    return PSF_OK;
+}
 
 int psf_exact(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
     return run_forward(p, kExact, b, out, (cudaStream_t)stream);

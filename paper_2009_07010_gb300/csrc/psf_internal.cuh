@@ -127,4 +127,23 @@ cudaError_t launch_zero_cutouts(float *out, const int64_t *offs, const int32_t *
 const DevObs *plan_devobs(psf_plan_t p);
 uint32_t plan_flags(psf_plan_t p);
 
+// ---- gridded image-plane approximation (k_grid.cu) -------------------------
+// One pair of positions of the gridded transform: c = (coefficient of a', coefficient
+// of b', rho, 0) of Algorithm 1's half phase change A = alpha (c.x a' + c.y b') and
+// B = beta rho; output offsets in floats, off1 < 0 when the pair has one position.
+struct GridPair {
+    float4 c0, c1;
+    long long off0, off1;
+};
+
+bool img_grid_supported(int N);
+cudaError_t launch_grid_cells(const double2 *bin_uv, const int2 *bin_samp, const int32_t *bin_first,
+                              const double2 *chan, const float *W, int nbl, int nout, double dt_raw, int N,
+                              double ncell, double *acc, double *glob, cudaStream_t st);
+cudaError_t launch_grid_dft(const float *P, double2 *Y, double2 *S, int N, cudaStream_t st);
+cudaError_t launch_grid_table(const double2 *S, const double *acc, const double *glob, int N, double du,
+                              float4 *G, cudaStream_t st);
+cudaError_t launch_img_grid(const float4 *G, const GridPair *pairs, int npairs, int N, float *out, int nsm,
+                            cudaStream_t st);
+
 }  // namespace psf

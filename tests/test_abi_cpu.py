@@ -44,8 +44,9 @@ def test_null_handles(L):
     assert L.psf_plan_nvis(None) == -1
     L.psf_plan_destroy(None)
     b = _lib.BatchT(0, None, None, 0, 1e-5, None)
-    for fn in (L.psf_exact, L.psf_approx_uv, L.psf_approx_img):
+    for fn in (L.psf_exact, L.psf_approx_uv, L.psf_approx_img, L.psf_approx_img_grid):
         assert fn(None, ctypes.byref(b), None, None) == _lib.PSF_EINVAL
+    assert L.psf_img_grid_table(None, 64, 1e-5, None, None) == _lib.PSF_EINVAL
     assert L.psf_approx_uv_img(None, ctypes.byref(b), None, None, None) == _lib.PSF_EINVAL
     assert L.psf_adjoint(None, 0, ctypes.byref(b), None, None, None, None) == _lib.PSF_EINVAL
     assert L.psf_sync_status(None, None) == _lib.PSF_EINVAL
