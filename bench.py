@@ -190,8 +190,15 @@ def parity_check(psf):
             for m, got in (("uv", guv), ("img", gimg)):
                 got = got.cpu().numpy().astype(np.float64)
                 res[f"{prec}/{m}_fused"] = float(np.max(np.abs(got - refs[m])) / np.max(np.abs(refs[m])))
+        # Method 2 in the gridded form of Eq. 45 against the oracle's gridded form
+        gref = oracle.psf_img_grid(obs, bg.lm, int(bg.npix[0]), bg.cell_rad).ravel()
+        for prec in ("fp32", "tc_fp16"):
+            plan.set_opts(prec=prec)
+            got = plan.approx_img_grid(batch).cpu().numpy().astype(np.float64)
+            res[f"{prec}/img_grid"] = float(np.max(np.abs(got - gref)) / np.max(np.abs(gref)))
     return {"workload": "16ant_1km_1h_4ch_64px", "metric": "max |P - P_oracle| / max |P_oracle|", "err_max": res,
-            "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3}}
+            "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3, "fp32/img_grid": 1e-5,
+                          "tc_fp16/img_grid": 3e-4}}
 
 
 def cpu_baseline_sample(obs, batch):
@@ -273,6 +280,94 @@ def measure_batched(psf, prec, steps=2, which="c4"):
             "adjoint_exact": adj}
 
 
+# Executed warp-instructions per position of k_img_grid (ncu smsp__inst_executed.sum of one
+# launch / positions; profiles/k_img_grid_radial16384.md), for the kernel source below.
+PROFILED_GRID = {"kernel_sha256_prefix": "f623518e68ad870c", "inst_per_position": {128: 214640640 / 4096, 64: 44775424 / 4096}}
+
+
+def grid_inst_per_position(N):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2009_07010_gb300", "csrc", "k_grid.cu")
+    h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    if h != PROFILED_GRID["kernel_sha256_prefix"]:
+        return None
+    return PROFILED_GRID["inst_per_position"].get(N)
+
+
+def measure_img_grid(psf, plan, obs, clocks, npos=16384):
+    """Method 2 in the gridded form of Eq. 45 on the benchmark observation: npos positions
+    of the radial grid out to 3 degrees, cutouts of 128 and 64 pixels at 1.5".  The
+    position-independent table (effective PSF, its DFT, per-cell means) is built by the
+    first call and kept; the timed calls evaluate Algorithm 1 on the uv cells and one
+    inverse FFT per position.  Also: per-position cost against the visibility-level
+    Method 2 and the gridding error (max |grid - img| / max |img|) at sampled radii."""
+    import torch
+    peaks, src = load_peaks()
+    lm = obsgen.config5_batch().lm[:npos]
+    cell = obsgen.config2_batch().cell_rad
+    sm_mhz = (clocks or {}).get("sm_mhz") or 1900.0
+    res = {}
+    for N in (128, 64):
+        b = psf.Batch(lm, N, cell)
+        out = torch.empty(b.total(), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plan.approx_img_grid(b, out=out)
+        torch.cuda.synchronize()
+        build_ms = (time.perf_counter() - t0) * 1e3
+        plan.approx_img_grid(b, out=out)
+        torch.cuda.synchronize()
+        plan.profile_read()
+        plan.profile_enable(True)
+        nrep = 5
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(nrep):
+            plan.approx_img_grid(b, out=out)
+        e1.record()
+        torch.cuda.synchronize()
+        kms, nkc, _ = plan.profile_read()
+        plan.profile_enable(False)
+        call_ms = e0.elapsed_time(e1) / nrep
+        kms /= nrep
+        gbs = 4.0 * N * N * npos / (kms * 1e-3) / 1e9
+        ipp = grid_inst_per_position(N)
+        roof = {"bound": "alu", "unit": "warp-instructions/s",
+                "peak": 152 * 4 * sm_mhz * 1e6, "peak_source": "152 SMs x 4 issue slots x median SM clock",
+                "inst_per_position": ipp,
+                "achieved": None if ipp is None else ipp * npos / (kms * 1e-3),
+                "hbm_output_gbs": gbs, "hbm_output_frac": gbs / peaks["hbm_gbs"], "hbm_peak_source": src}
+        roof["frac"] = None if roof["achieved"] is None else roof["achieved"] / roof["peak"]
+        res[f"{N}px"] = {"positions": npos, "table_build_ms": build_ms, "call_ms": call_ms, "kernel_ms": kms,
+                         "positions_per_s": npos / (call_ms * 1e-3), "kernel_positions_per_s": npos / (kms * 1e-3),
+                         "roofline": roof}
+    # visibility-level Method 2 at sampled radii: cost per position and the gridding error
+    sel = np.array([127, 127 * 4 + 42, 128 * 64 + 127 - 64, 128 * 127 + 5])
+    sel = sel[sel < npos]
+    N = 128
+    bs = psf.Batch(lm[sel], N, cell)
+    grid = plan.approx_img_grid(bs).cpu().numpy().astype(np.float64).reshape(len(sel), N, N)
+    img_out = torch.empty(bs.total(), dtype=torch.float32, device="cuda")
+    plan.approx_img(bs, out=img_out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    plan.approx_img(bs, out=img_out)
+    e1.record()
+    torch.cuda.synchronize()
+    img_ms = e0.elapsed_time(e1) / len(sel)
+    img = img_out.cpu().numpy().astype(np.float64).reshape(len(sel), N, N)
+    r_deg = np.degrees(np.arcsin(np.hypot(lm[sel, 0], lm[sel, 1])))
+    gap = {f"{r:.3f}deg": float(np.max(np.abs(grid[k] - img[k])) / np.max(np.abs(img[k])))
+           for k, r in enumerate(r_deg)}
+    per_pos_grid = 1e3 / res["128px"]["kernel_positions_per_s"]
+    return {"workload": "meerkat64_4h_16ch_radial16384pos_1p5arcsec", "nvis": obs.nvis(),
+            "kernel": "k_img_grid (Algorithm 1 on uv cells + inverse FFT per position, FP32)",
+            "sizes": res, "img_visibility_level_ms_per_128px_position": img_ms,
+            "cost_ratio_img_over_grid_128px": img_ms / per_pos_grid,
+            "gridding_error_vs_img_128px": gap}
+
+
 def measure_c5(psf, prec, nang=2, nrad=128):
     """Approximations vs exact on the approximation workload (64-antenna 8 km array,
     4 h at 8 s bins, 256 x 3.34375 MHz channels averaged 4:1 -> 232 243 200
@@ -342,6 +437,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-grid", action="store_true")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures); c4: only the batched "
@@ -461,6 +557,7 @@ def main():
         e2e = {"value": world * terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "ms_per_step": dt * 1e3}
 
+    img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
@@ -490,7 +587,7 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -189,7 +189,7 @@ int psf_approx_img_grid(psf_plan_t plan, const psf_batch_t *batch, float *out_de
 
 /* Diagnostic: the position-independent table psf_approx_img_grid uses for (npix,
  * cell_rad) in the plan's precision (built if needed), copied to table_dev (device
- * float32 [npix][npix][4]).  Entry [a][b] belongs to the cell at ((a - N/2) du,
+ * float32 [npix][npix][4]).  Entry [b][a] belongs to the cell at ((a - N/2) du,
  * (b - N/2) du), du = 1/(N cell_rad): (Re S, Im S) with S = F{P} / N^2, then
  * omega_E dt_c du and (Dnu/nu)_c |u_c| (dt_c, (Dnu/nu)_c the cell's mean interval and
  * fractional bandwidth).  Errors as psf_approx_img_grid. */

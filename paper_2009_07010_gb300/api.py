@@ -125,7 +125,7 @@ class Plan:
         return self.forward("img_grid", batch, out, stream)
 
     def img_grid_table(self, npix: int, cell: float, stream=None) -> torch.Tensor:
-        """Diagnostic: the gridded form's table [npix(a), npix(b), 4] (Re S, Im S,
+        """Diagnostic: the gridded form's table [npix(b), npix(a), 4] (Re S, Im S,
         omega_E dt_c du, (dnu/nu)_c |u_c|)."""
         t = torch.empty((npix, npix, 4), dtype=torch.float32, device="cuda")
         check(_lib.lib().psf_img_grid_table(self._h, int(npix), float(cell), ctypes.c_void_p(t.data_ptr()),

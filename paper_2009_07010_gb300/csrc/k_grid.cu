@@ -16,19 +16,17 @@
 //      the means over all visibilities (k_grid_cells, FP64 sums); the nearest-cell
 //      decision a' = floor(u_k N cell + 0.5), u_k = ubar nu_r / c, is taken in FP64
 //      with IEEE round-to-nearest operations in exactly that order,
-//   the table G[a][b] = (Re S, Im S, alpha, beta), alpha = omega_E dt_c du and
+//   the table G[b][a] = (Re S, Im S, alpha, beta), alpha = omega_E dt_c du and
 //      beta = (dnu/nu)_c |u_c|, so that Algorithm 1's half phase changes are
 //      A = alpha (a' m0 - b' l0) (theta = atan2(v, u); (b' m0 - a' l0) for the literal
 //      arctan(u/v)) and B = beta rho (k_grid_table).
-// Per pair of positions (k_img_grid): X = S (D_0 + i D_1) with D_p = sinc(A_p) sinc(B_p).
-// The cutout is the real part of F^-1{S D}; with S Hermitian that equals F^-1{S D'} where
-// D' averages D over each cell and its mirror modulo N, which differs from D only on the
-// Nyquist row and column (a' or b' = -N/2, their own mirrors).  S D' is Hermitian, so the
-// inverse transform of X has the cutout of position 0 as its real part and that of
-// position 1 as its imaginary part.  The N x N inverse FFT runs in
-// shared memory as two passes (rows, then columns) of radix R1 x R2 Cooley-Tukey with
-// the small DFTs in registers; D is evaluated inside the first stage, and the last stage
-// writes both cutouts straight to global memory.
+// Per position (k_img_grid): D = sinc(A) sinc(B) on the cells and the real part of
+// F^-1{S D}.  With S Hermitian, that real part is F^-1{S D'} where D' averages D over
+// each cell and its mirror modulo N; D' differs from D only on the Nyquist row and
+// column (a' or b' = -N/2, their own mirrors).  S D' is Hermitian, so the transform runs
+// on half the cells: column transforms over b, then per row a real-output transform
+// built from one complex transform of half the length, all in shared memory with the
+// small DFTs in registers.
 #include <cuda_runtime.h>
 
 #include "psf_internal.cuh"
@@ -154,7 +152,7 @@ __global__ void k_grid_dft_cols(const double2 *__restrict__ Y, double2 *__restri
     }
 }
 
-// G[a N + b] = (Re S / N^2, Im S / N^2, omega_E dt_c du, (dnu/nu)_c |u_c|) for cell (a, b).
+// G[b N + a] = (Re S / N^2, Im S / N^2, omega_E dt_c du, (dnu/nu)_c |u_c|) for cell (a, b).
 __global__ void k_grid_table(const double2 *__restrict__ S, const double *__restrict__ acc,
                              const double *__restrict__ glob, int N, double du, float4 *__restrict__ G) {
     const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,27 +164,28 @@ __global__ void k_grid_table(const double2 *__restrict__ S, const double *__rest
     const double r = sw > 0 ? acc[3 * q + 2] / sw : (gw > 0 ? glob[2] / gw : 0.0);
     const double ua = (a - N / 2) * du, vb = (b - N / 2) * du;
     const double inv = 1.0 / ((double)N * N);
-    G[(int64_t)a * N + b] = make_float4((float)(S[q].x * inv), (float)(S[q].y * inv), (float)(kOmegaE * dt * du),
+    G[q] = make_float4((float)(S[q].x * inv), (float)(S[q].y * inv), (float)(kOmegaE * dt * du),
                                         (float)(r * sqrt(ua * ua + vb * vb)));
 }
 
 // ------------------------------------------------------------------ per-position transform
 
 // sinc_pi(x) = sin(pi x) / (pi x) = (-1)^n [sin(pi f) / (pi f)] (f / x), x = n + f, |f| <= 1/2.
-// The bracket is its Taylor series in (pi f)^2 to order 12 (truncation error < 5e-10).
+// n comes from adding 1.5 * 2^23 (|x| < 2^22), which rounds x to the nearest integer and
+// leaves the parity of n in the lowest mantissa bit; the bracket is its Taylor series in
+// (pi f)^2 to order 10 (truncation error < 4e-8).
 __device__ __forceinline__ float sinc_fast(float x) {
-    const float n = rintf(x);
+    const float t = x + 12582912.0f;
+    const float n = t - 12582912.0f;
     const float f = x - n;
     const float z = f * f;
-    float q = fmaf(z, 1.4842879e-4f, -2.3460810e-3f);
-    q = fmaf(z, q, 2.6147848e-2f);
+    float q = fmaf(z, -2.3460810e-3f, 2.6147848e-2f);
     q = fmaf(z, q, -1.9075182e-1f);
     q = fmaf(z, q, 8.1174243e-1f);
     q = fmaf(z, q, -1.6449341f);
     q = fmaf(z, q, 1.0f);
-    const int ni = (int)n;
-    if (ni != 0) q *= __fdividef(f, x);
-    return (ni & 1) ? -q : q;
+    if (n != 0.0f) q *= __fdividef(f, x);
+    return __int_as_float(__float_as_int(q) ^ (__float_as_int(t) << 31));
 }
 
 __host__ __device__ constexpr int ilog2(int r) { return r <= 1 ? 0 : 1 + ilog2(r / 2); }
@@ -224,11 +223,11 @@ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// In-register inverse DFT y[k] = sum_n x[n] exp(+2 pi i n k / R), R in {4, 8, 16}:
+// In-register inverse DFT y[k] = sum_n x[n] exp(+2 pi i n k / R), R in {2, 4, 8, 16}:
 // radix-2 decimation in time, natural order in and out.
 template <int R>
 __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
-    static_assert(R == 4 || R == 8 || R == 16, "radix");
+    static_assert(R == 2 || R == 4 || R == 8 || R == 16, "radix");
     float2 t[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) t[bitrev(i, R)] = x[i];
@@ -249,36 +248,47 @@ __device__ __forceinline__ void dft_reg(float2 (&x)[R]) {
     for (int i = 0; i < R; ++i) x[i] = t[i];
 }
 
+// Shapes: the column transforms (length N over b) run as R1 x R2 Cooley-Tukey, the row
+// transforms (length M = N/2, the complex core of each real row) as Q1 x Q2; T threads;
+// the second stages of both passes take their lines in P parts to bound registers.
 template <int N>
 struct GridFft;
 template <>
-struct GridFft<16> { static constexpr int R1 = 4, R2 = 4, T = 64; };
+struct GridFft<16> { static constexpr int R1 = 4, R2 = 4, Q1 = 4, Q2 = 2, T = 64, P = 1; };
 template <>
-struct GridFft<32> { static constexpr int R1 = 8, R2 = 4, T = 128; };
+struct GridFft<32> { static constexpr int R1 = 8, R2 = 4, Q1 = 4, Q2 = 4, T = 128, P = 1; };
 template <>
-struct GridFft<64> { static constexpr int R1 = 8, R2 = 8, T = 256; };
+struct GridFft<64> { static constexpr int R1 = 8, R2 = 8, Q1 = 8, Q2 = 4, T = 128, P = 1; };
 template <>
-struct GridFft<128> { static constexpr int R1 = 16, R2 = 8, T = 512; };
+struct GridFft<128> { static constexpr int R1 = 16, R2 = 8, Q1 = 8, Q2 = 8, T = 256, P = 2; };
 
 template <int N>
-constexpr int grid_smem_bytes() { return (N * (N + 1) + N) * (int)sizeof(float2); }
+constexpr int grid_smem_bytes() { return (N * (N / 2 + 1) + N) * (int)sizeof(float2); }
 
-// One CTA per pair of positions (grid-stride over pairs).  Shared memory: X [N][N + 1]
-// complex (row b = v cell / output row j, column a = u cell / output column i; the pad
-// keeps row-wise and column-wise lane patterns free of bank conflicts) and the N
-// twiddles exp(+2 pi i m / N).  Cell and pixel index origins are at N/2:
-// exp(2 pi i (a - N/2)(i - N/2) / N) = (-1)^(a + i) exp(2 pi i a i / N) for N % 4 == 0,
-// so X carries (-1)^(a + b) and the output (-1)^(i + j).
 template <int N>
-__global__ void __launch_bounds__(GridFft<N>::T) k_img_grid(const float4 *__restrict__ G,
-                                                            const GridPair *__restrict__ pairs, int npairs,
-                                                            float *__restrict__ out) {
-    constexpr int R1 = GridFft<N>::R1, R2 = GridFft<N>::R2, T = GridFft<N>::T, LD = N + 1;
-    constexpr int NA = N * R2 / T;   // items (line, n2) per thread in the first stage of a pass
-    constexpr int NB = N * R1 / T;   // items (line, k1) per thread in the second stage
-    static_assert(R1 * R2 == N && NA * T == N * R2 && NB * T == N * R1, "shape");
+constexpr int grid_min_blocks() { return N == 128 ? 3 : N == 64 ? 6 : 8; }
+
+// One CTA per position (grid-stride).  X = (-1)^(a+b) S D' is Hermitian, so only the
+// cells a in [0, N/2] are formed, in shared memory Z [N rows][N/2 + 1] (row b, later
+// output row j; the odd row stride keeps every lane pattern below free of bank
+// conflicts), with the N twiddles exp(+2 pi i m / N).
+//   (0) X on the half grid, flat over its cells
+//   (1) columns: length-N inverse DFT over b for a in [0, N/2); column 0 carries
+//       X[.][0] + i X[.][N/2], whose transforms are both real, and is unpacked into them
+//   (2) rows: each row j is Hermitian in a, and its real inverse DFT x is obtained from
+//       one length-N/2 complex DFT of C[k] = E[k] + i O[k], E[k] = Z[k] + conj Z[N/2 - k],
+//       O[k] = (Z[k] - conj Z[N/2 - k]) exp(2 pi i k / N): it returns x[2n] + i x[2n+1]
+//   (3) out[j][i] = (-1)^(i + j) x[i], two floats per store.
+// Cell and pixel index origins are at N/2: exp(2 pi i (a - N/2)(i - N/2) / N) =
+// (-1)^(a + i) exp(2 pi i a i / N) for N % 4 == 0.
+template <int N>
+__global__ void __launch_bounds__(GridFft<N>::T, grid_min_blocks<N>())
+    k_img_grid(const float4 *__restrict__ G, const GridPos *__restrict__ pos, int npos, float *__restrict__ out) {
+    using F = GridFft<N>;
+    constexpr int M = N / 2, LD = M + 1, T = F::T, R1 = F::R1, R2 = F::R2, Q1 = F::Q1, Q2 = F::Q2, P = F::P;
+    static_assert(R1 * R2 == N && Q1 * Q2 == M && M % P == 0 && N % P == 0, "shape");
     extern __shared__ float2 smem[];
-    float2 *X = smem;
+    float2 *Z = smem;
     float2 *tw = smem + N * LD;
     for (int m = threadIdx.x; m < N; m += T) {
         float s, c;
@@ -286,93 +296,176 @@ __global__ void __launch_bounds__(GridFft<N>::T) k_img_grid(const float4 *__rest
         tw[m] = make_float2(c, s);
     }
     __syncthreads();
-    for (int pr = blockIdx.x; pr < npairs; pr += gridDim.x) {
-        const GridPair pp = pairs[pr];
-        // pass 1 (rows b), stage a: X = S (D_0 + i D_1) (-1)^(a+b) on the cells a = n2 + R2 n1,
-        // R1-point DFT over n1, twiddle exp(2 pi i n2 k1 / N), stored at a = n2 + R2 k1
+    for (int p = blockIdx.x; p < npos; p += gridDim.x) {
+        const GridPos gp = pos[p];
+        // (0) X = (-1)^(a+b) S D' on the cells a in [0, M]; D' = D except on the Nyquist
+        // row and column, where it is averaged with the mirror cell modulo N.  Columns
+        // a < M: a fixed per thread, rows b0, b0 + RS, ... (RS even: the sign is fixed too);
+        // column M: one row per thread.
+        {
+            constexpr int RS = T / M;
+            static_assert(T % M == 0 && RS % 2 == 0 && T >= N, "pre-pass shape");
+            const int a = threadIdx.x % M, b0 = threadIdx.x / M;
+            const float af = (float)(a - M), lin0 = af * gp.c.x, cb = gp.c.y, rho = gp.c.z;
+            const float sg = ((a + b0) & 1) ? -1.f : 1.f;
+#pragma unroll 4
+            for (int b = b0; b < N; b += RS) {
+                const float4 g = __ldg(G + b * N + a);
+                const float bf = (float)(b - M);
+                float e = sinc_fast(g.z * fmaf(bf, cb, lin0));
+                if (a == 0 || b == 0) {
+                    const float ma = a == 0 ? af : -af, mb = b == 0 ? bf : -bf;
+                    e = 0.5f * (e + sinc_fast(g.z * fmaf(ma, gp.c.x, mb * cb)));
+                }
+                const float d = sg * e * sinc_fast(g.w * rho);
+                Z[b * LD + a] = make_float2(g.x * d, g.y * d);
+            }
+            for (int b = threadIdx.x; b < N; b += T) {
+                const float4 g = __ldg(G + b * N + M);
+                const float bf = (float)(b - M);
+                // a' = 0: the mirror (0, -b') has the same D (D is even), so D' = D here
+                float d = sinc_fast(g.z * (bf * cb)) * sinc_fast(g.w * rho);
+                if ((M + b) & 1) d = -d;
+                Z[b * LD + M] = make_float2(g.x * d, g.y * d);
+            }
+        }
+        __syncthreads();
+        // (1a) columns a in [0, M): R1-point DFT over b = n2 + R2 n1, twiddle
+        // exp(2 pi i n2 k1 / N), stored in place at rows n2 + R2 k1
 #pragma unroll 1
-        for (int q = 0; q < NA; ++q) {
-            const int it = threadIdx.x + q * T;
-            const int b = it % N, n2 = it / N;
-            const float bf = (float)(b - N / 2);
-            const float t0 = bf * pp.c0.y, t1 = bf * pp.c1.y;
+        for (int it = threadIdx.x; it < M * R2; it += T) {
+            const int a = it % M, n2 = it / M;
             float2 x[R1];
 #pragma unroll
             for (int n1 = 0; n1 < R1; ++n1) {
-                const int a = n2 + R2 * n1;
-                const float4 g = __ldg(G + a * N + b);
-                const float af = (float)(a - N / 2);
-                float e0 = sinc_fast(g.z * fmaf(af, pp.c0.x, t0));
-                float e1 = sinc_fast(g.z * fmaf(af, pp.c1.x, t1));
-                if (a == 0 || b == 0) {
-                    // Nyquist row / column: the cell is its own mirror modulo N, and the real
-                    // part of the inverse transform averages D over u and its alias
-                    const float ma = a == 0 ? af : -af, mb = b == 0 ? bf : -bf;
-                    e0 = 0.5f * (e0 + sinc_fast(g.z * fmaf(ma, pp.c0.x, mb * pp.c0.y)));
-                    e1 = 0.5f * (e1 + sinc_fast(g.z * fmaf(ma, pp.c1.x, mb * pp.c1.y)));
+                const int r = (n2 + R2 * n1) * LD;
+                float2 v = Z[r + a];
+                if (a == 0) {
+                    const float2 w = Z[r + M];
+                    v = make_float2(v.x - w.y, v.y + w.x);
                 }
-                const float d0 = e0 * sinc_fast(g.w * pp.c0.z), d1 = e1 * sinc_fast(g.w * pp.c1.z);
-                float xr = g.x * d0 - g.y * d1, xi = g.y * d0 + g.x * d1;
-                if ((a + b) & 1) {
-                    xr = -xr;
-                    xi = -xi;
-                }
-                x[n1] = make_float2(xr, xi);
+                x[n1] = v;
             }
             dft_reg<R1>(x);
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) X[b * LD + n2 + R2 * k1] = cmul(x[k1], tw[n2 * k1]);
+            for (int k1 = 0; k1 < R1; ++k1) Z[(n2 + R2 * k1) * LD + a] = cmul(x[k1], tw[n2 * k1]);
         }
         __syncthreads();
-        // pass 1, stage b: R2-point DFT over n2 for each (b, k1); output column k1 + R1 k2
-        {
-            float2 y[NB][R2];
+        // (1b) R2-point DFT over n2 for each (a, k1); output rows j = k1 + R1 k2.  A part's
+        // reads all precede its writes; parts touch disjoint columns (column M belongs to
+        // the part holding column 0).
+#pragma unroll 1
+        for (int part = 0; part < P; ++part) {
+            constexpr int LA = M / P, NI = LA * R1, K = (NI + T - 1) / T;
+            float2 y[K][R2];
 #pragma unroll
-            for (int q = 0; q < NB; ++q) {
+            for (int q = 0; q < K; ++q) {
                 const int it = threadIdx.x + q * T;
-                const int b = it % N, k1 = it / N;
+                if (it < NI) {
+                    const int a = part * LA + it % LA, k1 = it / LA;
 #pragma unroll
-                for (int n2 = 0; n2 < R2; ++n2) y[q][n2] = X[b * LD + R2 * k1 + n2];
+                    for (int n2 = 0; n2 < R2; ++n2) y[q][n2] = Z[(R2 * k1 + n2) * LD + a];
+                }
             }
             __syncthreads();
 #pragma unroll
-            for (int q = 0; q < NB; ++q) {
+            for (int q = 0; q < K; ++q) {
                 const int it = threadIdx.x + q * T;
-                const int b = it % N, k1 = it / N;
-                dft_reg<R2>(y[q]);
+                if (it < NI) {
+                    const int a = part * LA + it % LA, k1 = it / LA;
+                    dft_reg<R2>(y[q]);
 #pragma unroll
-                for (int k2 = 0; k2 < R2; ++k2) X[b * LD + k1 + R1 * k2] = y[q][k2];
+                    for (int k2 = 0; k2 < R2; ++k2) {
+                        const int r = (k1 + R1 * k2) * LD;
+                        if (a == 0) {
+                            Z[r] = make_float2(y[q][k2].x, 0.f);
+                            Z[r + M] = make_float2(y[q][k2].y, 0.f);
+                        } else {
+                            Z[r + a] = y[q][k2];
+                        }
+                    }
+                }
             }
         }
         __syncthreads();
-        // pass 2 (columns i), stage a: rows n2 + R2 n1, in place
+        // (2a) rows j: C[k] for k = n2 + Q2 n1, Q1-point DFT over n1, twiddle
+        // exp(2 pi i n2 k1 / M) = tw[2 n2 k1], stored at k = n2 + Q2 k1 (parts = row ranges)
 #pragma unroll 1
-        for (int q = 0; q < NA; ++q) {
-            const int it = threadIdx.x + q * T;
-            const int i = it % N, n2 = it / N;
-            float2 x[R1];
+        for (int part = 0; part < P; ++part) {
+            constexpr int LJ = N / P, NI = LJ * Q2, K = (NI + T - 1) / T;
+            float2 c[K][Q1];
 #pragma unroll
-            for (int n1 = 0; n1 < R1; ++n1) x[n1] = X[(n2 + R2 * n1) * LD + i];
-            dft_reg<R1>(x);
+            for (int q = 0; q < K; ++q) {
+                const int it = threadIdx.x + q * T;
+                if (it < NI) {
+                    const int j = part * LJ + it % LJ, n2 = it / LJ;
 #pragma unroll
-            for (int k1 = 0; k1 < R1; ++k1) X[(n2 + R2 * k1) * LD + i] = cmul(x[k1], tw[n2 * k1]);
+                    for (int n1 = 0; n1 < Q1; ++n1) {
+                        const int k = n2 + Q2 * n1;
+                        const float2 zk = Z[j * LD + k], zm = Z[j * LD + M - k];
+                        const float2 e = make_float2(zk.x + zm.x, zk.y - zm.y);
+                        const float2 o = cmul(make_float2(zk.x - zm.x, zk.y + zm.y), tw[k]);
+                        c[q][n1] = make_float2(e.x - o.y, e.y + o.x);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const int it = threadIdx.x + q * T;
+                if (it < NI) {
+                    const int j = part * LJ + it % LJ, n2 = it / LJ;
+                    dft_reg<Q1>(c[q]);
+#pragma unroll
+                    for (int k1 = 0; k1 < Q1; ++k1) Z[j * LD + n2 + Q2 * k1] = cmul(c[q][k1], tw[2 * n2 * k1]);
+                }
+            }
         }
         __syncthreads();
-        // pass 2, stage b: rows j = k1 + R1 k2 of both cutouts, streamed to global memory
+        // (2b) Q2-point DFT over n2 for each (j, k1): y[k1 + Q1 k2] = x[2n] + i x[2n+1],
+        // n = k1 + Q1 k2, stored at slot n of row j
 #pragma unroll 1
-        for (int q = 0; q < NB; ++q) {
-            const int it = threadIdx.x + q * T;
-            const int i = it % N, k1 = it / N;
-            float2 y[R2];
+        for (int part = 0; part < P; ++part) {
+            constexpr int LJ = N / P, NI = LJ * Q1, K = (NI + T - 1) / T;
+            float2 y[K][Q2];
 #pragma unroll
-            for (int n2 = 0; n2 < R2; ++n2) y[n2] = X[(R2 * k1 + n2) * LD + i];
-            dft_reg<R2>(y);
+            for (int q = 0; q < K; ++q) {
+                const int it = threadIdx.x + q * T;
+                if (it < NI) {
+                    const int j = part * LJ + it % LJ, k1 = it / LJ;
 #pragma unroll
-            for (int k2 = 0; k2 < R2; ++k2) {
-                const int j = k1 + R1 * k2;
-                const float sg = ((i + j) & 1) ? -1.f : 1.f;
-                __stcs(out + pp.off0 + (int64_t)j * N + i, sg * y[k2].x);
-                if (pp.off1 >= 0) __stcs(out + pp.off1 + (int64_t)j * N + i, sg * y[k2].y);
+                    for (int n2 = 0; n2 < Q2; ++n2) y[q][n2] = Z[j * LD + Q2 * k1 + n2];
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int q = 0; q < K; ++q) {
+                const int it = threadIdx.x + q * T;
+                if (it < NI) {
+                    const int j = part * LJ + it % LJ, k1 = it / LJ;
+                    dft_reg<Q2>(y[q]);
+#pragma unroll
+                    for (int k2 = 0; k2 < Q2; ++k2) Z[j * LD + k1 + Q1 * k2] = y[q][k2];
+                }
+            }
+        }
+        __syncthreads();
+        // (3) out[j][2n], out[j][2n + 1] = (-1)^j (Re y[n], -Im y[n]), streamed
+        float *o = out + gp.off;
+        if ((gp.off & 1) == 0) {
+            for (int it = threadIdx.x; it < N * M; it += T) {
+                const int j = it / M, n = it % M;
+                const float2 y = Z[j * LD + n];
+                const float sg = (j & 1) ? -1.f : 1.f;
+                __stcs(reinterpret_cast<float2 *>(o + j * N + 2 * n), make_float2(sg * y.x, -sg * y.y));
+            }
+        } else {
+            for (int it = threadIdx.x; it < N * M; it += T) {
+                const int j = it / M, n = it % M;
+                const float2 y = Z[j * LD + n];
+                const float sg = (j & 1) ? -1.f : 1.f;
+                __stcs(o + j * N + 2 * n, sg * y.x);
+                __stcs(o + j * N + 2 * n + 1, -sg * y.y);
             }
         }
         __syncthreads();
@@ -380,8 +473,7 @@ __global__ void __launch_bounds__(GridFft<N>::T) k_img_grid(const float4 *__rest
 }
 
 template <int N>
-cudaError_t launch_img_grid_n(const float4 *G, const GridPair *pairs, int npairs, float *out, int nsm,
-                              cudaStream_t st) {
+cudaError_t launch_img_grid_n(const float4 *G, const GridPos *pos, int npos, float *out, int nsm, cudaStream_t st) {
     constexpr int smem = grid_smem_bytes<N>();
     static bool attr = false;
     if (!attr) {
@@ -392,8 +484,8 @@ cudaError_t launch_img_grid_n(const float4 *G, const GridPair *pairs, int npairs
     int per_sm = 1;
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_img_grid<N>, GridFft<N>::T, smem);
     if (e != cudaSuccess) return e;
-    const int grid = (int)std::min<int64_t>(npairs, (int64_t)nsm * std::max(1, per_sm) * 8);
-    k_img_grid<N><<<grid, GridFft<N>::T, smem, st>>>(G, pairs, npairs, out);
+    const int grid = (int)std::min<int64_t>(npos, (int64_t)nsm * std::max(1, per_sm) * 4);
+    k_img_grid<N><<<grid, GridFft<N>::T, smem, st>>>(G, pos, npos, out);
     return cudaGetLastError();
 }
 
@@ -428,14 +520,14 @@ cudaError_t launch_grid_table(const double2 *S, const double *acc, const double 
     return cudaGetLastError();
 }
 
-cudaError_t launch_img_grid(const float4 *G, const GridPair *pairs, int npairs, int N, float *out, int nsm,
+cudaError_t launch_img_grid(const float4 *G, const GridPos *pos, int npos, int N, float *out, int nsm,
                             cudaStream_t st) {
-    if (npairs <= 0) return cudaSuccess;
+    if (npos <= 0) return cudaSuccess;
     switch (N) {
-        case 16: return launch_img_grid_n<16>(G, pairs, npairs, out, nsm, st);
-        case 32: return launch_img_grid_n<32>(G, pairs, npairs, out, nsm, st);
-        case 64: return launch_img_grid_n<64>(G, pairs, npairs, out, nsm, st);
-        case 128: return launch_img_grid_n<128>(G, pairs, npairs, out, nsm, st);
+        case 16: return launch_img_grid_n<16>(G, pos, npos, out, nsm, st);
+        case 32: return launch_img_grid_n<32>(G, pos, npos, out, nsm, st);
+        case 64: return launch_img_grid_n<64>(G, pos, npos, out, nsm, st);
+        case 128: return launch_img_grid_n<128>(G, pos, npos, out, nsm, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -1009,32 +1009,22 @@ int run_img_grid(psf_plan_s *p, const psf_batch_t *b, float *out, cudaStream_t s
         return literal ? make_float4((float)-l0, (float)m0, rho, 0.f) : make_float4((float)m0, (float)-l0, rho, 0.f);
     };
     static const int kSizes[] = {16, 32, 64, 128};
-    std::vector<GridPair> pairs;
+    std::vector<GridPos> gpos;
     int start[4] = {0, 0, 0, 0}, count[4] = {0, 0, 0, 0};
     const float4 *G[4] = {nullptr, nullptr, nullptr, nullptr};
     for (int t = 0; t < 4; ++t) {
-        std::vector<int> idx;
+        start[t] = (int)gpos.size();
         for (int i = 0; i < h.npos; ++i)
-            if (h.npix[i] == kSizes[t]) idx.push_back(i);
-        if (idx.empty()) continue;
-        if ((s = grid_tables(p, kSizes[t], h.cell, st, &G[t]))) return s;
-        start[t] = (int)pairs.size();
-        for (size_t k = 0; k < idx.size(); k += 2) {
-            GridPair gp{};
-            gp.c0 = coef(idx[k]);
-            gp.off0 = h.out_off[idx[k]];
-            if (k + 1 < idx.size()) {
-                gp.c1 = coef(idx[k + 1]);
-                gp.off1 = h.out_off[idx[k + 1]];
-            } else {
-                gp.c1 = make_float4(0.f, 0.f, 0.f, 0.f);
-                gp.off1 = -1;
+            if (h.npix[i] == kSizes[t]) {
+                GridPos g{};
+                g.c = coef(i);
+                g.off = h.out_off[i];
+                gpos.push_back(g);
             }
-            pairs.push_back(gp);
-        }
-        count[t] = (int)pairs.size() - start[t];
+        count[t] = (int)gpos.size() - start[t];
+        if (count[t] && (s = grid_tables(p, kSizes[t], h.cell, st, &G[t]))) return s;
     }
-    if ((s = upload_meta(p, pairs.data(), pairs.size() * sizeof(GridPair), st))) return s;
+    if ((s = upload_meta(p, gpos.data(), gpos.size() * sizeof(GridPos), st))) return s;
     for (int t = 0; t < 4; ++t) {
         if (!count[t]) continue;
         cudaEvent_t ev1 = nullptr, ev2 = nullptr;
@@ -1050,7 +1040,7 @@ int run_img_grid(psf_plan_s *p, const psf_batch_t *b, float *out, cudaStream_t s
             p->prof_used++;
             PSF_TRY(cudaEventRecord(ev1, st));
         }
-        PSF_TRY(launch_img_grid(G[t], (const GridPair *)p->meta.p + start[t], count[t], kSizes[t], out, p->nsm, st));
+        PSF_TRY(launch_img_grid(G[t], (const GridPos *)p->meta.p + start[t], count[t], kSizes[t], out, p->nsm, st));
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
         p->n_kernels++;

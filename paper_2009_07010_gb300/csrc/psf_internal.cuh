@@ -128,12 +128,13 @@ const DevObs *plan_devobs(psf_plan_t p);
 uint32_t plan_flags(psf_plan_t p);
 
 // ---- gridded image-plane approximation (k_grid.cu) -------------------------
-// One pair of positions of the gridded transform: c = (coefficient of a', coefficient
-// of b', rho, 0) of Algorithm 1's half phase change A = alpha (c.x a' + c.y b') and
-// B = beta rho; output offsets in floats, off1 < 0 when the pair has one position.
-struct GridPair {
-    float4 c0, c1;
-    long long off0, off1;
+// One position of the gridded transform: c = (coefficient of a', coefficient of b',
+// rho, 0) of Algorithm 1's half phase changes A = alpha (c.x a' + c.y b') and
+// B = beta rho; off = float offset of the cutout in the output.
+struct GridPos {
+    float4 c;
+    long long off;
+    long long pad;
 };
 
 bool img_grid_supported(int N);
@@ -143,7 +144,7 @@ cudaError_t launch_grid_cells(const double2 *bin_uv, const int2 *bin_samp, const
 cudaError_t launch_grid_dft(const float *P, double2 *Y, double2 *S, int N, cudaStream_t st);
 cudaError_t launch_grid_table(const double2 *S, const double *acc, const double *glob, int N, double du,
                               float4 *G, cudaStream_t st);
-cudaError_t launch_img_grid(const float4 *G, const GridPair *pairs, int npairs, int N, float *out, int nsm,
+cudaError_t launch_img_grid(const float4 *G, const GridPos *pos, int npos, int N, float *out, int nsm,
                             cudaStream_t st);
 
 }  // namespace psf

@@ -44,8 +44,8 @@ def _c1_ref(flags):
 @pytest.mark.parametrize("prec", ["fp32", "tc_fp16"])
 @pytest.mark.parametrize("literal", [False, True])
 def test_grid_config1_every_pixel(psf, prec, literal):
-    """Workload 1 (16 antennas, 64 x 64 at 2"): five positions (an odd count, so the last
-    pair holds one), every pixel against the oracle, both readings of theta."""
+    """Workload 1 (16 antennas, 64 x 64 at 2"): five positions, every pixel against the
+    oracle, both readings of theta."""
     flags = psf.PSF_IMG_LITERAL_THETA if literal else 0
     obs = obsgen.config1_obs()
     ref = _c1_ref(flags)
@@ -125,13 +125,13 @@ def test_grid_cell_table_bda_full_size(psf):
     N, cell = 64, 1.5 * ARCSEC
     ref = oracle.grid_tables(obs, N, cell, cells_only=True)
     with psf.Plan(obs, prec="tc_fp16") as plan:
-        t = plan.img_grid_table(N, cell).cpu().numpy().astype(np.float64)   # [a][b][4]
+        t = plan.img_grid_table(N, cell).cpu().numpy().astype(np.float64)   # [b][a][4]
         assert plan.sync_status() == 0
     du = 1.0 / (N * cell)
-    dt = t[:, :, 2].T / (OMEGA_E * du)                                       # -> [b][a]
+    dt = t[:, :, 2] / (OMEGA_E * du)
     a = (np.arange(N) - N // 2) * du
     uabs = np.hypot(a[None, :], a[:, None])
-    r = np.where(uabs > 0, t[:, :, 3].T / np.where(uabs > 0, uabs, 1), ref["r"])
+    r = np.where(uabs > 0, t[:, :, 3] / np.where(uabs > 0, uabs, 1), ref["r"])
     assert (ref["wsum"] > 0).sum() > N * N // 4
     np.testing.assert_allclose(dt, ref["dt"], rtol=2e-6)
     np.testing.assert_allclose(r, ref["r"], rtol=2e-6)
@@ -146,7 +146,7 @@ def test_grid_transform_of_effective_psf(psf):
     with psf.Plan(obs, prec="fp32") as plan:
         P = plan.approx_img(psf.Batch(np.zeros((1, 2)), N, cell)).cpu().numpy().astype(np.float64).reshape(N, N)
         t = plan.img_grid_table(N, cell).cpu().numpy().astype(np.float64)
-    S = (t[:, :, 0] + 1j * t[:, :, 1]).T
+    S = t[:, :, 0] + 1j * t[:, :, 1]
     ref = np.fft.fftshift(np.fft.fft2(np.fft.ifftshift(P))) / N ** 2
     assert np.max(np.abs(S - ref)) <= 1e-6 * np.max(np.abs(ref))
 
