@@ -438,10 +438,13 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grid", action="store_true")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5"],
+    ap.add_argument("--grid-positions", type=int, default=16384,
+                    help="positions of the gridded-form measurement (radial grid out to 3 deg)")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures); c4: only the batched "
-                         "256 x 64^2 measurement (profiler captures of the batched kernel)")
+                         "256 x 64^2 measurement (profiler captures of the batched kernel); grid: only "
+                         "the gridded Method 2 measurement on the benchmark observation")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -452,6 +455,18 @@ def main():
         psf.build_library()
         torch.cuda.set_device(local)
         print(json.dumps(measure_batched(psf, args.prec, steps=args.steps, which=args.workload)), flush=True)
+        return 0
+    if args.workload == "grid":
+        import torch
+        import paper_2009_07010_gb300 as psf
+        psf.build_library()
+        torch.cuda.set_device(local)
+        obs = obsgen.config2_obs()
+        with psf.Plan(obs, prec=args.prec) as plan:
+            res = measure_img_grid(psf, plan, obs, None, npos=args.grid_positions)
+            if plan.sync_status() != 0:
+                raise RuntimeError("device-side error in the gridded-form measurement")
+        print(json.dumps(res), flush=True)
         return 0
     if args.workload == "c5":
         import torch
@@ -557,7 +572,8 @@ def main():
         e2e = {"value": world * terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "ms_per_step": dt * 1e3}
 
-    img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks)
+    img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks,
+                                                                       npos=args.grid_positions)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
