@@ -81,6 +81,7 @@ extern "C" {
 #define PSF_METHOD_EXACT 0
 #define PSF_METHOD_UV    1
 #define PSF_METHOD_IMG   2
+#define PSF_METHOD_IMG_GRID 3   /* Method 2 in the gridded form of psf_approx_img_grid; psf_clean only */
 
 typedef struct psf_plan_s *psf_plan_t;
 
@@ -194,6 +195,41 @@ int psf_approx_img_grid(psf_plan_t plan, const psf_batch_t *batch, float *out_de
  * omega_E dt_c du and (Dnu/nu)_c |u_c| (dt_c, (Dnu/nu)_c the cell's mean interval and
  * fractional bandwidth).  Errors as psf_approx_img_grid. */
 int psf_img_grid_table(psf_plan_t plan, int npix, double cell_rad, float *table_dev, void *cuda_stream);
+
+/* Hogbom CLEAN with position-dependent PSFs (Algorithm 2).  The image has nl columns
+ * (l) and nm rows (m), both even; pixel (x, y) is the direction ((x - nl/2) cell_rad,
+ * (y - nm/2) cell_rad), so pixel (nl/2, nm/2) is the phase centre.  Each iteration
+ * takes the peak pixel l0 = argmax I_D (signed maximum; the first in row-major order
+ * among equal values), evaluates the psf_npix x psf_npix cutout of `method`
+ * (PSF_METHOD_EXACT, _UV, _IMG or _IMG_GRID, in the plan's precision and flags) at l0,
+ * normalises it to 1 at its centre pixel, subtracts gain * I_D(l0) times it from I_D on
+ * the window around l0 (clipped to the image) and adds gain * I_D(l0) to the model at
+ * l0.  As the algorithm's do-while: the first iteration always runs (max_iter >= 1),
+ * each later one only while the peak exceeds threshold, at most max_iter in all. */
+typedef struct {
+    int32_t nl, nm;        /* image size in pixels (columns, rows), even */
+    double cell_rad;       /* pixel size (direction-cosine units), > 0 */
+    int32_t psf_npix;      /* PSF cutout size N: even, 2..4096 (16, 32, 64, 128 for IMG_GRID) */
+    int32_t method;        /* PSF_METHOD_* */
+    float gain;            /* CLEAN gain gamma, 0 < gain <= 1 */
+    float threshold;       /* stop once the peak residual is <= threshold */
+    int32_t max_iter;      /* >= 0 */
+    int32_t reserved;
+} psf_clean_t;
+
+/* Runs the loop of psf_clean_t on the device and returns when it has stopped (the
+ * stream is synchronized).  residual_dev: device float32 [nm][nl], in: the dirty image,
+ * out: the residual.  model_dev: device float32 [nm][nl] or NULL; components are added
+ * to it (it is not cleared).  comp_pix_dev / comp_flux_dev: device int32 / float32
+ * [max_iter] or NULL: per iteration the peak pixel index y * nl + x and the subtracted
+ * flux gain * I_D(l0).  *niter_out (host, may be NULL): iterations performed.  With
+ * PSF_METHOD_IMG_GRID every step stays on the device and the host reads the loop
+ * record once per 64 queued iterations; the other methods read the peak record back
+ * each iteration to place the cutout.  Errors: PSF_EINVAL (sizes, gain, method, NULL
+ * residual), PSF_EUNSUPPORTED (a cutout size the method does not support,
+ * PSF_COMPLEX_OUT), and those of the PSF calls. */
+int psf_clean(psf_plan_t plan, const psf_clean_t *cfg, float *residual_dev, float *model_dev,
+              int32_t *comp_pix_dev, float *comp_flux_dev, int32_t *niter_out, void *cuda_stream);
 
 /* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
  * adjoint: given dL/dP (device float32, same layout as the forward output) it

@@ -200,3 +200,49 @@ def psf_img_grid(obs, lm, npix: int, cell: float, flags: int = 0) -> np.ndarray:
     if _load().or_psf_img_grid(*o.args(), lm.shape[0], _p(lm), N, float(cell), int(flags), _p(out)) != 0:
         raise ValueError("invalid observation or grid")
     return out
+
+
+def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: float, max_iter: int,
+          flags: int = 0):
+    """Hogbom CLEAN with position-dependent PSFs (Algorithm 2), float64.
+
+    dirty [nm, nl]: the dirty image; pixel (nl/2, nm/2) is the phase centre, pixel (x, y)
+    the direction ((x - nl/2) cell, (y - nm/2) cell).  Each iteration takes the peak pixel
+    l0 = argmax(I_D) (the first of equal maxima in row-major order), the PSF cutout of
+    `method` ('exact' | 'uv' | 'img' | 'img_grid') at l0, normalised to 1 at its centre
+    pixel, and subtracts gain * I_D(l0) times it from I_D around l0 (clipped to the image),
+    adding gain * I_D(l0) to the model at l0.  As the algorithm's do-while, the first
+    iteration always runs and each later one only while the peak exceeds threshold.
+    Returns (residual, model, [(pixel index y * nl + x, flux), ...])."""
+    res = np.array(dirty, np.float64, copy=True)
+    nm, nl = res.shape
+    model = np.zeros_like(res)
+    comps = []
+    N = int(npix)
+    mid = {"exact": EXACT, "uv": UV, "img": IMG}
+    for it in range(int(max_iter)):
+        idx = int(np.argmax(res))
+        y, x = divmod(idx, nl)
+        peak = float(res[y, x])
+        if it > 0 and not peak > threshold:
+            break
+        l0, m0 = (x - nl // 2) * cell, (y - nm // 2) * cell
+        if method == "img_grid":
+            P = psf_img_grid(obs, [[l0, m0]], N, cell, flags=flags)[0]
+        else:
+            class _B:
+                pass
+            b = _B()
+            b.lm = np.array([[l0, m0]])
+            b.npix = np.array([N], np.int32)
+            b.cell_rad = cell
+            P = psf(obs, mid[method], b, flags=flags).reshape(N, N)
+        P = P / P[N // 2, N // 2]
+        g = gain * peak
+        y0, x0 = y - N // 2, x - N // 2
+        ya, yb = max(y0, 0), min(y0 + N, nm)
+        xa, xb = max(x0, 0), min(x0 + N, nl)
+        res[ya:yb, xa:xb] -= g * P[ya - y0:yb - y0, xa - x0:xb - x0]
+        model[y, x] += g
+        comps.append((idx, g))
+    return res, model, comps

@@ -15,12 +15,18 @@ PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_EUNSUPPORTED, PSF_ETIMEOUT = 0, -
 PSF_FP32, PSF_TC_FP16, PSF_TC_BF16 = 0, 1, 3
 PSF_WTERM, PSF_IMG_LITERAL_THETA, PSF_DETERMINISTIC, PSF_COMPLEX_OUT = 1, 2, 4, 8
 PSF_ALGO_AUTO, PSF_ALGO_CUTOUT = 0, 1
-EXACT, UV, IMG = 0, 1, 2
+EXACT, UV, IMG, IMG_GRID = 0, 1, 2, 3
 
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
-           "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
+           "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_clean", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
            "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
+
+
+class CleanT(ctypes.Structure):
+    _fields_ = [("nl", ctypes.c_int32), ("nm", ctypes.c_int32), ("cell_rad", ctypes.c_double),
+                ("psf_npix", ctypes.c_int32), ("method", ctypes.c_int32), ("gain", ctypes.c_float),
+                ("threshold", ctypes.c_float), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class PsfError(RuntimeError):
@@ -76,6 +82,8 @@ def lib(auto_build: bool = False):
                 f = getattr(L, name)
                 f.argtypes = [P, ctypes.POINTER(BatchT), P, P]
                 f.restype = I
+            L.psf_clean.argtypes = [P, ctypes.POINTER(CleanT), P, P, P, P, ctypes.POINTER(ctypes.c_int32), P]
+            L.psf_clean.restype = I
             L.psf_img_grid_table.argtypes = [P, I, ctypes.c_double, P, P]
             L.psf_img_grid_table.restype = I
             L.psf_approx_uv_img.argtypes = [P, ctypes.POINTER(BatchT), P, P, P]

@@ -132,6 +132,26 @@ class Plan:
                                             _stream_handle(stream)), "psf_img_grid_table")
         return t
 
+    def clean(self, dirty: torch.Tensor, cell: float, npix: int, method: str = "img_grid", gain: float = 0.1,
+              threshold: float = 0.0, max_iter: int = 1000, model: Optional[torch.Tensor] = None, stream=None):
+        """Hogbom CLEAN with position-dependent PSFs (Algorithm 2) on the device.  dirty:
+        float32 CUDA tensor [nm, nl], overwritten with the residual.  Returns (residual,
+        model, component pixel indices [niter], component fluxes [niter])."""
+        assert dirty.dtype == torch.float32 and dirty.is_cuda and dirty.is_contiguous() and dirty.dim() == 2
+        nm, nl = dirty.shape
+        if model is None:
+            model = torch.zeros_like(dirty)
+        cpix = torch.empty(max(max_iter, 1), dtype=torch.int32, device=dirty.device)
+        cflux = torch.empty(max(max_iter, 1), dtype=torch.float32, device=dirty.device)
+        mcode = {"exact": _lib.EXACT, "uv": _lib.UV, "img": _lib.IMG, "img_grid": _lib.IMG_GRID}[method]
+        cfg = _lib.CleanT(nl, nm, float(cell), int(npix), mcode, float(gain), float(threshold), int(max_iter), 0)
+        n = ctypes.c_int32(0)
+        check(_lib.lib().psf_clean(self._h, ctypes.byref(cfg), ctypes.c_void_p(dirty.data_ptr()),
+                                   ctypes.c_void_p(model.data_ptr()), ctypes.c_void_p(cpix.data_ptr()),
+                                   ctypes.c_void_p(cflux.data_ptr()), ctypes.byref(n), _stream_handle(stream)),
+              "psf_clean")
+        return dirty, model, cpix[:n.value], cflux[:n.value]
+
     def approx_uv_img(self, batch: Batch, out_uv: Optional[torch.Tensor] = None,
                       out_img: Optional[torch.Tensor] = None, stream=None):
         """Methods 1 and 2 of one batch in one call: (uv cutouts, image-plane cutouts)."""

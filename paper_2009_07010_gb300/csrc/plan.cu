@@ -1048,6 +1048,81 @@ int run_img_grid(psf_plan_s *p, const psf_batch_t *b, float *out, cudaStream_t s
     return PSF_OK;
 }
 
+// Hogbom CLEAN with position-dependent PSFs (Algorithm 2).  With the gridded PSF every
+// step of an iteration is a kernel reading the device loop record (k_clean.cu), queued in
+// chunks; the other methods read the peak record back to place the cutout.
+int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int32_t *cpix, float *cflux,
+              int32_t *niter_out, cudaStream_t st) {
+    if (!c || !res) return PSF_EINVAL;
+    if (c->nl < 2 || c->nm < 2 || (c->nl & 1) || (c->nm & 1) || !(c->cell_rad > 0.0) || !(c->gain > 0.f) ||
+        !(c->gain <= 1.f) || c->max_iter < 0)
+        return PSF_EINVAL;
+    const int N = c->psf_npix;
+    if (N < 2 || N > 4096 || (N & 1)) return PSF_EINVAL;
+    if (c->method < kExact || c->method > PSF_METHOD_IMG_GRID) return PSF_EINVAL;
+    if ((int64_t)c->nl * c->nm >= (int64_t(1) << 31)) return PSF_EUNSUPPORTED;
+    if (p->opts.flags & PSF_COMPLEX_OUT) return PSF_EUNSUPPORTED;
+    if (c->method == PSF_METHOD_IMG_GRID && !img_grid_supported(N)) return PSF_EUNSUPPORTED;
+    if (niter_out) *niter_out = 0;
+    if (c->max_iter == 0) return PSF_OK;
+    const size_t ws_bytes = sizeof(CleanState) + 2 * sizeof(unsigned long long);
+    DevBuf ws, P;
+    PSF_TRY(ws.reserve(ws_bytes));
+    PSF_TRY(P.reserve((size_t)N * N * sizeof(float)));
+    PSF_TRY(cudaMemsetAsync(ws.p, 0, ws_bytes, st));
+    CleanState *sd = (CleanState *)ws.p;
+    unsigned long long *key = (unsigned long long *)((char *)ws.p + sizeof(CleanState));
+    const int literal = (p->opts.flags & PSF_IMG_LITERAL_THETA) ? 1 : 0;
+    const int64_t npx = (int64_t)c->nl * c->nm;
+    CleanState h{};
+    int64_t t = 0;
+    if (c->method == PSF_METHOD_IMG_GRID) {
+        const float4 *G = nullptr;
+        int s = grid_tables(p, N, c->cell_rad, st, &G);
+        if (s) return s;
+        constexpr int kChunk = 64;
+        for (;;) {
+            for (int q = 0; q < kChunk; ++q, ++t) {
+                PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
+                PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
+                                          c->threshold, c->max_iter, literal, st));
+                PSF_TRY(launch_img_grid(G, &sd->gpos, 1, N, (float *)P.p, p->nsm, st));
+                PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
+                                         st));
+            }
+            if (p->prof) p->n_kernels += 4 * kChunk;
+            PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
+            PSF_TRY(cudaStreamSynchronize(st));
+            if (h.done) break;
+        }
+    } else {
+        double lm[2] = {0.0, 0.0};
+        psf_batch_t b{};
+        b.npos = 1;
+        b.lm = lm;
+        b.npix0 = N;
+        b.cell_rad = c->cell_rad;
+        for (;; ++t) {
+            PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
+            PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
+                                      c->threshold, c->max_iter, literal, st));
+            if (p->prof) p->n_kernels += 2;
+            PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
+            PSF_TRY(cudaStreamSynchronize(st));
+            if (!h.active) break;
+            const int x = h.pix % c->nl, y = h.pix / c->nl;
+            lm[0] = (x - c->nl / 2) * c->cell_rad;
+            lm[1] = (y - c->nm / 2) * c->cell_rad;
+            int s = run_forward(p, c->method, &b, (float *)P.p, st);
+            if (s) return s;
+            PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux, st));
+            if (p->prof) p->n_kernels += 1;
+        }
+    }
+    if (niter_out) *niter_out = h.iter;
+    return PSF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1055,6 +1130,12 @@ extern "C" {
 int psf_approx_img_grid(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
     if (!p || !out) return PSF_EINVAL;
     return run_img_grid(p, b, out, (cudaStream_t)stream);
+}
+
+int psf_clean(psf_plan_t p, const psf_clean_t *cfg, float *residual, float *model, int32_t *comp_pix,
+              float *comp_flux, int32_t *niter_out, void *stream) {
+    if (!p) return PSF_EINVAL;
+    return run_clean(p, cfg, residual, model, comp_pix, comp_flux, niter_out, (cudaStream_t)stream);
 }
 
 int psf_img_grid_table(psf_plan_t p, int npix, double cell_rad, float *table_dev, void *stream) {

@@ -147,4 +147,23 @@ cudaError_t launch_grid_table(const double2 *S, const double *acc, const double 
 cudaError_t launch_img_grid(const float4 *G, const GridPos *pos, int npos, int N, float *out, int nsm,
                             cudaStream_t st);
 
+// ---- Hogbom CLEAN (k_clean.cu) ------------------------------------------------
+// Device record of the CLEAN loop (one per call).
+struct CleanState {
+    GridPos gpos;     // position record of the gridded PSF at the current peak (offset 0)
+    int32_t done;     // 1 once the loop has stopped
+    int32_t iter;     // iterations performed
+    int32_t active;   // the current iteration subtracts
+    int32_t pix;      // peak pixel y * nl + x
+    float peak;       // I_D at the peak
+    int32_t pad[3];
+};
+
+cudaError_t launch_clean_argmax(const float *res, int64_t n, const CleanState *st, unsigned long long *key, int nsm,
+                                cudaStream_t s);
+cudaError_t launch_clean_prep(const unsigned long long *key, unsigned long long *key_next, CleanState *st, int nl,
+                              int nm, double cell, float threshold, int max_iter, int literal, cudaStream_t s);
+cudaError_t launch_clean_sub(float *res, float *model, const float *P, CleanState *st, int nl, int nm, int N,
+                             float gain, int32_t *comp_pix, float *comp_flux, cudaStream_t s);
+
 }  // namespace psf
