@@ -368,6 +368,45 @@ def measure_img_grid(psf, plan, obs, clocks, npos=16384):
             "gridding_error_vs_img_128px": gap}
 
 
+def measure_clean(psf, plan, nl=2048, nsrc=200, npix=128, gain=0.1, iters=None):
+    """Hogbom CLEAN with position-dependent PSFs (Algorithm 2) on the benchmark
+    observation: an nl x nl image at 1.5" centred on (0.03, 0.03) holding nsrc seeded
+    point sources (fluxes 1 / U^1.5 capped at 100, positions uniform), each shaped like the
+    device's gridded PSF at its pixel (a synthetic dirty image, truncated to the 128 x 128
+    window).  Per PSF method: iterations run and the mean time per iteration (argmax,
+    PSF at the peak, subtraction); the gridded PSF keeps every step on the device."""
+    import torch
+    rng = np.random.default_rng(obsgen.SEED_BASE + 7)
+    cell, centre, N = obsgen.config2_batch().cell_rad, (0.03, 0.03), npix
+    xs = rng.integers(N // 2, nl - N // 2, nsrc)
+    ys = rng.integers(N // 2, nl - N // 2, nsrc)
+    fl = np.minimum(rng.uniform(0.0, 1.0, nsrc) ** -1.5, 100.0)
+    lm = np.stack([centre[0] + (xs - nl // 2) * cell, centre[1] + (ys - nl // 2) * cell], axis=1)
+    P = plan.approx_img_grid(psf.Batch(lm, N, cell)).view(nsrc, N, N)
+    P = P / P[:, N // 2, N // 2].view(nsrc, 1, 1)
+    dirty = torch.zeros((nl, nl), dtype=torch.float32, device="cuda")
+    for k in range(nsrc):
+        dirty[ys[k] - N // 2:ys[k] + N // 2, xs[k] - N // 2:xs[k] + N // 2] += float(fl[k]) * P[k]
+    iters = iters or {"img_grid": 2000, "img": 8, "uv": 8, "exact": 4}
+    out = {}
+    for method, n in iters.items():
+        r = dirty.clone()
+        plan.clean(r.clone(), cell, N, method=method, gain=gain, max_iter=2, centre=centre)   # tables, warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, cp, _ = plan.clean(r, cell, N, method=method, gain=gain, threshold=0.0, max_iter=n, centre=centre)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[method] = {"iterations": int(len(cp)), "ms_per_iteration": dt * 1e3 / max(1, len(cp)),
+                       "iterations_per_s": len(cp) / dt}
+    if plan.sync_status() != 0:
+        raise RuntimeError("device-side error in the CLEAN measurement")
+    ref = out["exact"]["ms_per_iteration"]
+    return {"workload": f"meerkat64_4h_16ch_clean_{nl}px_{nsrc}src_psf{N}", "image": [nl, nl],
+            "psf_npix": N, "gain": gain, "sources": nsrc, "per_method": out,
+            "speedup_over_exact_per_iteration": {m: ref / v["ms_per_iteration"] for m, v in out.items()}}
+
+
 def measure_c5(psf, prec, nang=2, nrad=128):
     """Approximations vs exact on the approximation workload (64-antenna 8 km array,
     4 h at 8 s bins, 256 x 3.34375 MHz channels averaged 4:1 -> 232 243 200
@@ -438,13 +477,15 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grid", action="store_true")
+    ap.add_argument("--no-clean", action="store_true")
     ap.add_argument("--grid-positions", type=int, default=16384,
                     help="positions of the gridded-form measurement (radial grid out to 3 deg)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures); c4: only the batched "
                          "256 x 64^2 measurement (profiler captures of the batched kernel); grid: only "
-                         "the gridded Method 2 measurement on the benchmark observation")
+                         "the gridded Method 2 measurement on the benchmark observation; clean: only the "
+                         "CLEAN (Algorithm 2) measurement")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -455,6 +496,15 @@ def main():
         psf.build_library()
         torch.cuda.set_device(local)
         print(json.dumps(measure_batched(psf, args.prec, steps=args.steps, which=args.workload)), flush=True)
+        return 0
+    if args.workload == "clean":
+        import torch
+        import paper_2009_07010_gb300 as psf
+        psf.build_library()
+        torch.cuda.set_device(local)
+        with psf.Plan(obsgen.config2_obs(), prec=args.prec) as plan:
+            res = measure_clean(psf, plan)
+        print(json.dumps(res), flush=True)
         return 0
     if args.workload == "grid":
         import torch
@@ -574,6 +624,7 @@ def main():
 
     img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks,
                                                                        npos=args.grid_positions)
+    clean = None if args.no_clean or rank != 0 else measure_clean(psf, plan)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
@@ -603,7 +654,7 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

@@ -197,8 +197,9 @@ int psf_approx_img_grid(psf_plan_t plan, const psf_batch_t *batch, float *out_de
 int psf_img_grid_table(psf_plan_t plan, int npix, double cell_rad, float *table_dev, void *cuda_stream);
 
 /* Hogbom CLEAN with position-dependent PSFs (Algorithm 2).  The image has nl columns
- * (l) and nm rows (m), both even; pixel (x, y) is the direction ((x - nl/2) cell_rad,
- * (y - nm/2) cell_rad), so pixel (nl/2, nm/2) is the phase centre.  Each iteration
+ * (l) and nm rows (m), both even; pixel (x, y) is the direction (l_c + (x - nl/2)
+ * cell_rad, m_c + (y - nm/2) cell_rad): pixel (nl/2, nm/2) looks at (l_c, m_c), the phase
+ * centre for l_c = m_c = 0 or a facet's centre otherwise.  Each iteration
  * takes the peak pixel l0 = argmax I_D (signed maximum; the first in row-major order
  * among equal values), evaluates the psf_npix x psf_npix cutout of `method`
  * (PSF_METHOD_EXACT, _UV, _IMG or _IMG_GRID, in the plan's precision and flags) at l0,
@@ -209,6 +210,7 @@ int psf_img_grid_table(psf_plan_t plan, int npix, double cell_rad, float *table_
 typedef struct {
     int32_t nl, nm;        /* image size in pixels (columns, rows), even */
     double cell_rad;       /* pixel size (direction-cosine units), > 0 */
+    double l_c, m_c;       /* direction of pixel (nl/2, nm/2) */
     int32_t psf_npix;      /* PSF cutout size N: even, 2..4096 (16, 32, 64, 128 for IMG_GRID) */
     int32_t method;        /* PSF_METHOD_* */
     float gain;            /* CLEAN gain gamma, 0 < gain <= 1 */
@@ -230,6 +232,8 @@ typedef struct {
  * PSF_COMPLEX_OUT), and those of the PSF calls. */
 int psf_clean(psf_plan_t plan, const psf_clean_t *cfg, float *residual_dev, float *model_dev,
               int32_t *comp_pix_dev, float *comp_flux_dev, int32_t *niter_out, void *cuda_stream);
+/* (every pixel's direction must satisfy l^2 + m^2 < 1 where the loop places a cutout:
+ * PSF_EINVAL from the PSF call otherwise) */
 
 /* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
  * adjoint: given dL/dP (device float32, same layout as the forward output) it

@@ -69,6 +69,9 @@ def _load():
             lib.or_psf_img_grid.restype = ctypes.c_int
             lib.or_psf_img_grid.argtypes = obs_args + [ctypes.c_int, P, ctypes.c_int, ctypes.c_double,
                                                        ctypes.c_int, P]
+            lib.or_psf_img_grid_tables.restype = ctypes.c_int
+            lib.or_psf_img_grid_tables.argtypes = [ctypes.c_int, ctypes.c_double, P, P, P, ctypes.c_int, P,
+                                                   ctypes.c_int, P]
             lib.or_vjp.restype = ctypes.c_int
             lib.or_vjp.argtypes = obs_args + [ctypes.c_int, ctypes.c_int, P, P, ctypes.c_double,
                                               ctypes.c_int, P, P, P, P]
@@ -202,33 +205,64 @@ def psf_img_grid(obs, lm, npix: int, cell: float, flags: int = 0) -> np.ndarray:
     return out
 
 
+def psf_img_grid_from_tables(tables, lm, npix: int, cell: float, flags: int = 0) -> np.ndarray:
+    """psf_img_grid from the tables of grid_tables(obs, npix, cell) (computed once)."""
+    N = int(npix)
+    lm = np.ascontiguousarray(np.asarray(lm, np.float64).reshape(-1, 2))
+    S = np.ascontiguousarray(np.stack([tables["S"].real, tables["S"].imag], axis=-1))
+    dt = np.ascontiguousarray(tables["dt"])
+    r = np.ascontiguousarray(tables["r"])
+    out = np.empty((lm.shape[0], N, N))
+    if _load().or_psf_img_grid_tables(N, float(cell), _p(S), _p(dt), _p(r), lm.shape[0], _p(lm), int(flags),
+                                      _p(out)) != 0:
+        raise ValueError("invalid grid")
+    return out
+
+
 def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: float, max_iter: int,
-          flags: int = 0):
+          flags: int = 0, margins: bool = False, centre=(0.0, 0.0), follow=None):
     """Hogbom CLEAN with position-dependent PSFs (Algorithm 2), float64.
 
-    dirty [nm, nl]: the dirty image; pixel (nl/2, nm/2) is the phase centre, pixel (x, y)
-    the direction ((x - nl/2) cell, (y - nm/2) cell).  Each iteration takes the peak pixel
+    dirty [nm, nl]: the dirty image; pixel (x, y) is the direction (l_c + (x - nl/2) cell,
+    m_c + (y - nm/2) cell), (l_c, m_c) = centre.  Each iteration takes the peak pixel
     l0 = argmax(I_D) (the first of equal maxima in row-major order), the PSF cutout of
     `method` ('exact' | 'uv' | 'img' | 'img_grid') at l0, normalised to 1 at its centre
     pixel, and subtracts gain * I_D(l0) times it from I_D around l0 (clipped to the image),
     adding gain * I_D(l0) to the model at l0.  As the algorithm's do-while, the first
     iteration always runs and each later one only while the peak exceeds threshold.
-    Returns (residual, model, [(pixel index y * nl + x, flux), ...])."""
+    Returns (residual, model, [(pixel index y * nl + x, flux), ...]); with margins, also the
+    gap between each iteration's peak and the largest other pixel (how far each argmax
+    decision is from a tie).  With follow (a sequence of pixel indices), iteration k takes
+    pixel follow[k] instead of the argmax and runs len(follow) iterations without the
+    threshold test; the fourth return value is then [(max I_D, I_D at the pixel taken), ...]
+    per iteration, so that another implementation's choices can be checked against this
+    one's values (where two pixels are within rounding of each other, either is a correct
+    argmax)."""
     res = np.array(dirty, np.float64, copy=True)
     nm, nl = res.shape
     model = np.zeros_like(res)
-    comps = []
+    comps, gaps = [], []
     N = int(npix)
     mid = {"exact": EXACT, "uv": UV, "img": IMG}
-    for it in range(int(max_iter)):
-        idx = int(np.argmax(res))
+    tables = grid_tables(obs, N, cell) if method == "img_grid" else None
+    niter = int(max_iter) if follow is None else len(follow)
+    for it in range(niter):
+        if follow is None:
+            idx = int(np.argmax(res))
+        else:
+            idx = int(follow[it])
+            gaps.append((float(np.max(res)), float(res.flat[idx])))
         y, x = divmod(idx, nl)
         peak = float(res[y, x])
-        if it > 0 and not peak > threshold:
+        if follow is None and it > 0 and not peak > threshold:
             break
-        l0, m0 = (x - nl // 2) * cell, (y - nm // 2) * cell
+        if margins and follow is None:
+            res[y, x] = -np.inf
+            gaps.append(peak - float(np.max(res)))
+            res[y, x] = peak
+        l0, m0 = centre[0] + (x - nl // 2) * cell, centre[1] + (y - nm // 2) * cell
         if method == "img_grid":
-            P = psf_img_grid(obs, [[l0, m0]], N, cell, flags=flags)[0]
+            P = psf_img_grid_from_tables(tables, [[l0, m0]], N, cell, flags=flags)[0]
         else:
             class _B:
                 pass
@@ -245,4 +279,4 @@ def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: fl
         res[ya:yb, xa:xb] -= g * P[ya - y0:yb - y0, xa - x0:xb - x0]
         model[y, x] += g
         comps.append((idx, g))
-    return res, model, comps
+    return (res, model, comps, gaps) if (margins or follow is not None) else (res, model, comps)

@@ -494,46 +494,55 @@ int or_grid_tables(OR_OBS_ARGS, int N, double cell, double *S, double *dtc, doub
     return 0;
 }
 
-/* Gridded cutouts: out[p][j N + i] = (1/N^2) Re sum_b sum_a S[b][a] D_ab(l0_p)
- *                                      exp(2 pi i ((a-N/2)(i-N/2) + (b-N/2)(j-N/2)) / N),
+/* Gridded cutouts from the tables of or_grid_tables:
+ *   out[p][j N + i] = (1/N^2) Re sum_b sum_a S[b][a] D_ab(l0_p)
+ *                              exp(2 pi i ((a-N/2)(i-N/2) + (b-N/2)(j-N/2)) / N),
  * D_ab = Algorithm 1 at the cell centre with the cell's mean dt and dnu/nu. */
+int or_psf_img_grid_tables(int N, double cell, const double *S, const double *dtc, const double *rc, int npos,
+                           const double *lm, int flags, double *out) {
+    if (N < 2 || N % 2 || !(cell > 0)) return -1;
+    const int64_t NN = (int64_t)N * N;
+    double *twr = (double *)malloc(sizeof(double) * NN), *twi = (double *)malloc(sizeof(double) * NN);
+    double *Tr = (double *)malloc(sizeof(double) * NN), *Ti = (double *)malloc(sizeof(double) * NN);
+    or_grid_twiddles(N, twr, twi);
+    const double du = 1.0 / ((double)N * cell);
+    for (int p = 0; p < npos; ++p) {
+        double l0 = lm[2 * p], m0 = lm[2 * p + 1];
+        for (int64_t q = 0; q < NN; ++q) {
+            int a = (int)(q % N), b = (int)(q / N);
+            double D, Dl, Dm;
+            or_img_decorr((a - N / 2) * du, (b - N / 2) * du, dtc[q], rc[q], l0, m0, flags & OR_LITERAL_THETA,
+                          &D, &Dl, &Dm);
+            Tr[q] = S[2 * q] * D;
+            Ti[q] = S[2 * q + 1] * D;
+        }
+        double *op = out + (int64_t)p * NN;
+        #pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t q = 0; q < NN; ++q) {
+            int i = (int)(q % N), j = (int)(q / N);
+            double acc = 0;
+            for (int b = 0; b < N; ++b)
+                for (int a = 0; a < N; ++a) {
+                    double cr = twr[a * N + i] * twr[b * N + j] - twi[a * N + i] * twi[b * N + j];
+                    double ci = twr[a * N + i] * twi[b * N + j] + twi[a * N + i] * twr[b * N + j];
+                    acc += Tr[(int64_t)b * N + a] * cr - Ti[(int64_t)b * N + a] * ci;
+                }
+            op[q] = acc / (double)NN;
+        }
+    }
+    free(twr); free(twi); free(Tr); free(Ti);
+    return 0;
+}
+
+/* Gridded cutouts (Eq. 45 with Algorithm 1): the tables, then or_psf_img_grid_tables. */
 int or_psf_img_grid(OR_OBS_ARGS, int npos, const double *lm, int N, double cell, int flags, double *out) {
     if (N < 2 || N % 2 || !(cell > 0)) return -1;
     const int64_t NN = (int64_t)N * N;
     double *S = (double *)malloc(sizeof(double) * 2 * NN);
     double *dtc = (double *)malloc(sizeof(double) * NN), *rc = (double *)malloc(sizeof(double) * NN);
-    double *twr = (double *)malloc(sizeof(double) * NN), *twi = (double *)malloc(sizeof(double) * NN);
-    double *Tr = (double *)malloc(sizeof(double) * NN), *Ti = (double *)malloc(sizeof(double) * NN);
     int rc0 = or_grid_tables(nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights, N, cell,
                              S, dtc, rc, NULL, NULL);
-    if (rc0 == 0) {
-        or_grid_twiddles(N, twr, twi);
-        const double du = 1.0 / ((double)N * cell);
-        for (int p = 0; p < npos; ++p) {
-            double l0 = lm[2 * p], m0 = lm[2 * p + 1];
-            for (int64_t q = 0; q < NN; ++q) {
-                int a = (int)(q % N), b = (int)(q / N);
-                double D, Dl, Dm;
-                or_img_decorr((a - N / 2) * du, (b - N / 2) * du, dtc[q], rc[q], l0, m0, flags & OR_LITERAL_THETA,
-                              &D, &Dl, &Dm);
-                Tr[q] = S[2 * q] * D;
-                Ti[q] = S[2 * q + 1] * D;
-            }
-            double *op = out + (int64_t)p * NN;
-            #pragma omp parallel for schedule(dynamic, 1)
-            for (int64_t q = 0; q < NN; ++q) {
-                int i = (int)(q % N), j = (int)(q / N);
-                double acc = 0;
-                for (int b = 0; b < N; ++b)
-                    for (int a = 0; a < N; ++a) {
-                        double cr = twr[a * N + i] * twr[b * N + j] - twi[a * N + i] * twi[b * N + j];
-                        double ci = twr[a * N + i] * twi[b * N + j] + twi[a * N + i] * twr[b * N + j];
-                        acc += Tr[(int64_t)b * N + a] * cr - Ti[(int64_t)b * N + a] * ci;
-                    }
-                op[q] = acc / (double)NN;
-            }
-        }
-    }
-    free(S); free(dtc); free(rc); free(twr); free(twi); free(Tr); free(Ti);
+    if (rc0 == 0) rc0 = or_psf_img_grid_tables(N, cell, S, dtc, rc, npos, lm, flags, out);
+    free(S); free(dtc); free(rc);
     return rc0;
 }

@@ -25,7 +25,7 @@ EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_a
 
 class CleanT(ctypes.Structure):
     _fields_ = [("nl", ctypes.c_int32), ("nm", ctypes.c_int32), ("cell_rad", ctypes.c_double),
-                ("psf_npix", ctypes.c_int32), ("method", ctypes.c_int32), ("gain", ctypes.c_float),
+                ("l_c", ctypes.c_double), ("m_c", ctypes.c_double), ("psf_npix", ctypes.c_int32), ("method", ctypes.c_int32), ("gain", ctypes.c_float),
                 ("threshold", ctypes.c_float), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 

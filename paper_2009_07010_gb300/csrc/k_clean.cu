@@ -1,7 +1,7 @@
 // Hogbom CLEAN with position-dependent PSFs (Algorithm 2): the per-iteration kernels.
 //
 // One iteration on the residual image I_D [nm][nl] (pixel (x, y) is the direction
-// ((x - nl/2) cell, (y - nm/2) cell)):
+// (l_c + (x - nl/2) cell, m_c + (y - nm/2) cell)):
 //   k_clean_argmax  l0 = argmax I_D: every thread folds its pixels into a 64-bit key
 //                   (order-preserving bits of the value, then the complement of the
 //                   index, so that equal maxima resolve to the first pixel in row-major
@@ -62,8 +62,8 @@ __global__ void k_clean_argmax(const float *__restrict__ res, int64_t n, const C
 }
 
 __global__ void k_clean_prep(const unsigned long long *__restrict__ key, unsigned long long *__restrict__ key_next,
-                             CleanState *__restrict__ st, int nl, int nm, double cell, float threshold, int max_iter,
-                             int literal) {
+                             CleanState *__restrict__ st, int nl, int nm, double cell, double lc, double mc,
+                             float threshold, int max_iter, int literal) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     *key_next = 0ull;
     st->active = 0;
@@ -83,7 +83,7 @@ __global__ void k_clean_prep(const unsigned long long *__restrict__ key, unsigne
     st->pix = pix;
     st->peak = peak;
     const int x = pix % nl, y = pix / nl;
-    const double l0 = (x - nl / 2) * cell, m0 = (y - nm / 2) * cell;
+    const double l0 = lc + (x - nl / 2) * cell, m0 = mc + (y - nm / 2) * cell;
     const float rho = (float)sqrt(l0 * l0 + m0 * m0);
     st->gpos.c = literal ? make_float4((float)-l0, (float)m0, rho, 0.f) : make_float4((float)m0, (float)-l0, rho, 0.f);
     st->gpos.off = 0;
@@ -124,8 +124,9 @@ cudaError_t launch_clean_argmax(const float *res, int64_t n, const CleanState *s
 }
 
 cudaError_t launch_clean_prep(const unsigned long long *key, unsigned long long *key_next, CleanState *st, int nl,
-                              int nm, double cell, float threshold, int max_iter, int literal, cudaStream_t s) {
-    k_clean_prep<<<1, 32, 0, s>>>(key, key_next, st, nl, nm, cell, threshold, max_iter, literal);
+                              int nm, double cell, double lc, double mc, float threshold, int max_iter, int literal,
+                              cudaStream_t s) {
+    k_clean_prep<<<1, 32, 0, s>>>(key, key_next, st, nl, nm, cell, lc, mc, threshold, max_iter, literal);
     return cudaGetLastError();
 }
 

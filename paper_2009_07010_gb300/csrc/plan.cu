@@ -1060,6 +1060,7 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
     const int N = c->psf_npix;
     if (N < 2 || N > 4096 || (N & 1)) return PSF_EINVAL;
     if (c->method < kExact || c->method > PSF_METHOD_IMG_GRID) return PSF_EINVAL;
+    if (!std::isfinite(c->l_c) || !std::isfinite(c->m_c)) return PSF_EINVAL;
     if ((int64_t)c->nl * c->nm >= (int64_t(1) << 31)) return PSF_EUNSUPPORTED;
     if (p->opts.flags & PSF_COMPLEX_OUT) return PSF_EUNSUPPORTED;
     if (c->method == PSF_METHOD_IMG_GRID && !img_grid_supported(N)) return PSF_EUNSUPPORTED;
@@ -1085,7 +1086,7 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
             for (int q = 0; q < kChunk; ++q, ++t) {
                 PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
                 PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
-                                          c->threshold, c->max_iter, literal, st));
+                                          c->l_c, c->m_c, c->threshold, c->max_iter, literal, st));
                 PSF_TRY(launch_img_grid(G, &sd->gpos, 1, N, (float *)P.p, p->nsm, st));
                 PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
                                          st));
@@ -1105,14 +1106,14 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
         for (;; ++t) {
             PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
             PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
-                                      c->threshold, c->max_iter, literal, st));
+                                      c->l_c, c->m_c, c->threshold, c->max_iter, literal, st));
             if (p->prof) p->n_kernels += 2;
             PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
             PSF_TRY(cudaStreamSynchronize(st));
             if (!h.active) break;
             const int x = h.pix % c->nl, y = h.pix / c->nl;
-            lm[0] = (x - c->nl / 2) * c->cell_rad;
-            lm[1] = (y - c->nm / 2) * c->cell_rad;
+            lm[0] = c->l_c + (x - c->nl / 2) * c->cell_rad;
+            lm[1] = c->m_c + (y - c->nm / 2) * c->cell_rad;
             int s = run_forward(p, c->method, &b, (float *)P.p, st);
             if (s) return s;
             PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux, st));

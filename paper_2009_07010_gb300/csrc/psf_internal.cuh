@@ -162,7 +162,8 @@ struct CleanState {
 cudaError_t launch_clean_argmax(const float *res, int64_t n, const CleanState *st, unsigned long long *key, int nsm,
                                 cudaStream_t s);
 cudaError_t launch_clean_prep(const unsigned long long *key, unsigned long long *key_next, CleanState *st, int nl,
-                              int nm, double cell, float threshold, int max_iter, int literal, cudaStream_t s);
+                              int nm, double cell, double lc, double mc, float threshold, int max_iter, int literal,
+                              cudaStream_t s);
 cudaError_t launch_clean_sub(float *res, float *model, const float *P, CleanState *st, int nl, int nm, int N,
                              float gain, int32_t *comp_pix, float *comp_flux, cudaStream_t s);
 
