@@ -13,7 +13,8 @@ Parity status: every function here is pinned by ``tests/test_oracle_pins.py``
 (closed forms, limits, symmetries, brute force, finite differences) and, for the
 gridded image-plane form, ``tests/test_oracle_grid_pins.py`` (numpy FFT, exact
 agreement with the visibility-level Method 2 on cell-centred uv points, brute-force
-gridding, symmetry).  The
+gridding, symmetry) and, for Hogbom CLEAN (Algorithm 2, ``clean``),
+``tests/test_oracle_clean_pins.py`` (closed-form decay of isolated sources).  The
 accuracy levels the paper reads off its MeerKAT figures (Sect. 4, Figs. 4-7)
 are *parity unpinned*: they need the paper's array, dataset and imager.
 """
