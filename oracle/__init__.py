@@ -281,3 +281,59 @@ def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: fl
         model[y, x] += g
         comps.append((idx, g))
     return (res, model, comps, gaps) if (margins or follow is not None) else (res, model, comps)
+
+
+FWHM_STEP = 0.25   # profile sampling step along a direction, in pixels
+
+
+def _bilinear(P, x, y):
+    """P at (column x, row y) by bilinear interpolation; None outside [0, N-1]^2."""
+    N = P.shape[0]
+    i0, j0 = int(np.floor(x)), int(np.floor(y))
+    if i0 < 0 or j0 < 0 or i0 + 1 > N - 1 or j0 + 1 > N - 1:
+        if 0 <= x <= N - 1 and 0 <= y <= N - 1 and (x == N - 1 or y == N - 1):
+            i0, j0 = min(i0, N - 2), min(j0, N - 2)
+        else:
+            return None
+    fx, fy = x - i0, y - j0
+    return ((1 - fx) * (1 - fy) * P[j0, i0] + fx * (1 - fy) * P[j0, i0 + 1]
+            + (1 - fx) * fy * P[j0 + 1, i0] + fx * fy * P[j0 + 1, i0 + 1])
+
+
+def fwhm(P, l0: float, m0: float, cell: float):
+    """Full width at half maximum of a cutout along the radial and tangential directions
+    of its position (Sect. 2.3, Fig. 3), in direction-cosine units.
+
+    Half maximum h = half the centre pixel P[N/2, N/2] (the PSF at l0).  Along a unit
+    direction e (radial (l0, m0)/rho, tangential (-m0, l0)/rho; the l and m axes at
+    rho = 0) the profile v(t) = P(centre + t e) is taken by bilinear interpolation at
+    t = k FWHM_STEP pixels, k = 1, 2, ..., on each side; the first sample with v <= h
+    ends the walk and the crossing is interpolated linearly between it and the previous
+    sample.  FWHM = (t+ + t-) cell.  NaN if a walk leaves the cutout first."""
+    P = np.asarray(P, np.float64)
+    N = P.shape[0]
+    c = N // 2
+    h = 0.5 * P[c, c]
+    rho = float(np.hypot(l0, m0))
+    er = (l0 / rho, m0 / rho) if rho > 0 else (1.0, 0.0)
+    et = (-er[1], er[0])
+    out = []
+    for e in (er, et):
+        width = 0.0
+        for sgn in (1.0, -1.0):
+            prev, k, cross = float(P[c, c]), 1, None
+            while True:
+                t = k * FWHM_STEP
+                v = _bilinear(P, c + sgn * t * e[0], c + sgn * t * e[1])
+                if v is None:
+                    break
+                if v <= h:
+                    cross = t - FWHM_STEP + FWHM_STEP * (prev - h) / (prev - v)
+                    break
+                prev, k = v, k + 1
+            if cross is None:
+                width = np.nan
+                break
+            width += cross
+        out.append(width * cell)
+    return tuple(out)
