@@ -407,6 +407,30 @@ def measure_clean(psf, plan, nl=2048, nsrc=200, npix=128, gain=0.1, iters=None):
             "speedup_over_exact_per_iteration": {m: ref / v["ms_per_iteration"] for m, v in out.items()}}
 
 
+def measure_fwhm(psf, prec):
+    """PSF size against distance from the phase centre as in the paper's FWHM figure: the
+    64-antenna array at 1.4 GHz, 2 h of 1 s samples, 6 MHz of 50 kHz channels averaged
+    10 s x 1 MHz (CF 10x20) or 20 s x 2 MHz (CF 20x40); exact smeared PSFs (64 x 64 at 1")
+    at 0 to 4.5 deg, eight position angles each; FWHM along the radial and tangential
+    directions (psf_fwhm), mean over the angles, in arcsec."""
+    bg = obsgen.fig3_batch()
+    batch = psf.Batch.from_obsgen(bg)
+    r = np.degrees(np.arcsin(np.hypot(bg.lm[:, 0], bg.lm[:, 1])))
+    radii = sorted(set(np.round(r, 6)))
+    out = {}
+    for cf in ("10x20", "20x40"):
+        obs = obsgen.fig3_obs(cf)
+        with psf.Plan(obs, prec=prec) as plan:
+            w = plan.fwhm(batch, plan.exact(batch)).cpu().numpy() / (np.pi / 180 / 3600)
+            if plan.sync_status() != 0:
+                raise RuntimeError("device-side error in the FWHM measurement")
+        out[f"CF_{cf}"] = {"nvis": obs.nvis(),
+                           "radial_arcsec": {f"{d:.1f}deg": float(np.nanmean(w[np.abs(r - d) < 1e-6, 0])) for d in radii},
+                           "tangential_arcsec": {f"{d:.1f}deg": float(np.nanmean(w[np.abs(r - d) < 1e-6, 1])) for d in radii}}
+    return {"workload": "meerkat64_2h_1p4GHz_6MHz_fwhm", "method": "exact", "npix": 64, "cell_arcsec": 1.0,
+            "positions": bg.npos, **out}
+
+
 def measure_c5(psf, prec, nang=2, nrad=128):
     """Approximations vs exact on the approximation workload (64-antenna 8 km array,
     4 h at 8 s bins, 256 x 3.34375 MHz channels averaged 4:1 -> 232 243 200
@@ -478,6 +502,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-grid", action="store_true")
     ap.add_argument("--no-clean", action="store_true")
+    ap.add_argument("--no-fwhm", action="store_true")
     ap.add_argument("--grid-positions", type=int, default=16384,
                     help="positions of the gridded-form measurement (radial grid out to 3 deg)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean"],
@@ -625,6 +650,7 @@ def main():
     img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks,
                                                                        npos=args.grid_positions)
     clean = None if args.no_clean or rank != 0 else measure_clean(psf, plan)
+    fwhm = None if args.no_fwhm or rank != 0 else measure_fwhm(psf, args.prec)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
@@ -654,7 +680,7 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

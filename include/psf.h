@@ -235,6 +235,19 @@ int psf_clean(psf_plan_t plan, const psf_clean_t *cfg, float *residual_dev, floa
 /* (every pixel's direction must satisfy l^2 + m^2 < 1 where the loop places a cutout:
  * PSF_EINVAL from the PSF call otherwise) */
 
+/* Size of PSF cutouts as in Fig. 3: the full width at half maximum along the radial
+ * direction (l0, m0)/|l0| of each position and the tangential one perpendicular to it
+ * (the l and m axes at l0 = 0).  cutouts_dev: device float32 cutouts laid out as the
+ * batch describes (as written by psf_exact etc.); fwhm_dev: device float64 [npos][2]
+ * (radial, tangential) in direction-cosine units, overwritten.  Half maximum is half
+ * the centre pixel (the PSF at l0); on each side of the centre the profile is sampled by
+ * bilinear interpolation every quarter pixel up to the first sample at or below it, and
+ * the crossing is interpolated linearly from the previous sample; the width is the sum
+ * of both sides.  NaN where a profile leaves the cutout first.  Cutouts need N >= 4;
+ * errors as psf_exact's batch checks. */
+int psf_fwhm(psf_plan_t plan, const psf_batch_t *batch, const float *cutouts_dev, double *fwhm_dev,
+             void *cuda_stream);
+
 /* Vector-Jacobian product of the cutout map of `method` (PSF_METHOD_*), i.e. the
  * adjoint: given dL/dP (device float32, same layout as the forward output) it
  * writes dL/d(l0,m0) to dL_dlm_dev (device float64 [npos][2], overwritten) and,

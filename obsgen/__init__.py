@@ -206,6 +206,28 @@ def config5_batch(nrad: int = 128, nang: int = 128) -> Batch:
 
 
 # ------------------------------------------------------------ small cases
+def fig3_obs(cf: str = "20x40", every: int = 1) -> Observation:
+    """The setting of the paper's FWHM figure on the 64-antenna array (every `every`-th
+    antenna): 2 h of 1 s samples and 6 MHz of 50 kHz channels centred on 1.4 GHz, averaged
+    10 s x 1 MHz ("10x20") or 20 s x 2 MHz ("20x40")."""
+    tavg, favg = {"10x20": (10, 20), "20x40": (20, 40)}[cf]
+    return _obs(meerkat_like_array()[::every], 2 * 3600.0, tavg, 1.397e9, 50e3, 120, favg)
+
+
+def fig3_batch(npix: int = 64, cell_arcsec: float = 1.0, radii_deg=(0.0, 0.5, 1.0, 1.5, 2.0, 2.5, 3.0, 3.5, 4.0, 4.5),
+               nang: int = 8) -> Batch:
+    """Positions at the given distances from the phase centre, nang position angles each
+    (one at the centre), as in the FWHM-against-distance figure."""
+    lm = []
+    for r in radii_deg:
+        for k in range(1 if r == 0 else nang):
+            phi = 2.0 * np.pi * (k + 0.5) / nang
+            s = math.sin(r * DEG)
+            lm.append((s * math.cos(phi), s * math.sin(phi)))
+    lm = np.array(lm)
+    return Batch(lm, np.full(len(lm), npix, np.int32), cell_arcsec * ARCSEC)
+
+
 def tiny_obs(seed: int = 7, nant: int = 4, ntime: int = 24, nchan: int = 4,
              tavg=4, favg: int = 2, f0: float = 1.2e9, df: float = 2e6,
              dt: float = 2.0, radius_m: float = 3000.0,

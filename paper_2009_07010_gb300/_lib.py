@@ -19,7 +19,7 @@ EXACT, UV, IMG, IMG_GRID = 0, 1, 2, 3
 
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
-           "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_clean", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
+           "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_clean", "psf_fwhm", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
            "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
 
 
@@ -84,6 +84,8 @@ def lib(auto_build: bool = False):
                 f.restype = I
             L.psf_clean.argtypes = [P, ctypes.POINTER(CleanT), P, P, P, P, ctypes.POINTER(ctypes.c_int32), P]
             L.psf_clean.restype = I
+            L.psf_fwhm.argtypes = [P, ctypes.POINTER(BatchT), P, P, P]
+            L.psf_fwhm.restype = I
             L.psf_img_grid_table.argtypes = [P, I, ctypes.c_double, P, P]
             L.psf_img_grid_table.restype = I
             L.psf_approx_uv_img.argtypes = [P, ctypes.POINTER(BatchT), P, P, P]

@@ -155,6 +155,16 @@ class Plan:
               "psf_clean")
         return dirty, model, cpix[:n.value], cflux[:n.value]
 
+    def fwhm(self, batch: Batch, cutouts: torch.Tensor, stream=None) -> torch.Tensor:
+        """FWHM (radial, tangential) [npos, 2] float64 of the batch's cutouts (Fig. 3)."""
+        assert cutouts.dtype == torch.float32 and cutouts.is_cuda and cutouts.is_contiguous()
+        assert cutouts.numel() >= batch.total()
+        out = torch.empty((max(batch.npos, 1), 2), dtype=torch.float64, device=cutouts.device)
+        bs = batch.struct()
+        check(_lib.lib().psf_fwhm(self._h, ctypes.byref(bs), ctypes.c_void_p(cutouts.data_ptr()),
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "psf_fwhm")
+        return out[:batch.npos]
+
     def approx_uv_img(self, batch: Batch, out_uv: Optional[torch.Tensor] = None,
                       out_img: Optional[torch.Tensor] = None, stream=None):
         """Methods 1 and 2 of one batch in one call: (uv cutouts, image-plane cutouts)."""

@@ -69,7 +69,11 @@ __device__ __forceinline__ float dot3(float4 a, float4 L) { return a.x * L.x + a
 
 // Fast variants for weights that are rounded to FP16/BF16 afterwards (tensor-core
 // paths): the argument is reduced exactly to |r| <= 1/2 turn (x - rint(x)) and the
-// MUFU sine/cosine (__sinf, __sincosf, |error| ~ 1e-6 on [-pi, pi]) is used.
+// MUFU sine/cosine (__sinf, __sincosf) is used.  Its error bound is absolute (~4e-7 on
+// [-pi, pi]), so a ratio of two sines of small arguments is not taken from it: below
+// |pi y| = 0.1 (sinc) and |pi F r| = 0.1 (Dirichlet) the Taylor series of the ratio is
+// evaluated instead (truncation error < 3e-10); without this a sinc of a tiny argument
+// came out anywhere between 0 and 1 and the Dirichlet kernel as 0/0.
 __device__ __forceinline__ float sinpi_fast(float x) {   // sin(pi x)
     const float n = rintf(x * 0.5f);
     return __sinf(kPiF * (x - 2.0f * n));
@@ -79,15 +83,24 @@ __device__ __forceinline__ void sincospi2_fast(float x, float *s, float *c) {   
     __sincosf(2.0f * kPiF * r, s, c);
 }
 __device__ __forceinline__ float sincpi_fast(float y) {
-    return y == 0.0f ? 1.0f : sinpi_fast(y) / (kPiF * y);
+    const float x = kPiF * y;
+    if (fabsf(x) < 0.1f) {   // sin x / x = 1 - x^2/6 + x^4/120 - ...
+        const float x2 = x * x;
+        return 1.0f + x2 * (-1.0f / 6.0f + x2 * (1.0f / 120.0f));
+    }
+    return sinpi_fast(y) / x;
 }
 __device__ __forceinline__ float dirichlet_fast(int F, float a) {
     if (F == 1) return 1.0f;
     const float n = rintf(a);
     const float r = a - n;
     const float sgn = (((int)n * (F - 1)) & 1) ? -1.0f : 1.0f;
-    if (r == 0.0f) return sgn;
-    return sgn * sinpi_fast((float)F * r) / ((float)F * __sinf(kPiF * r));
+    const float Ff = (float)F, x = kPiF * r;
+    if (fabsf(Ff * x) < 0.1f) {   // sin(F x) / (F sin x) = 1 - (F^2-1) x^2/6 + (7/360 - F^2/36 + F^4/120) x^4
+        const float x2 = x * x, F2 = Ff * Ff;
+        return sgn * (1.0f + x2 * ((1.0f - F2) / 6.0f + x2 * (7.0f / 360.0f - F2 / 36.0f + F2 * F2 / 120.0f)));
+    }
+    return sgn * sinpi_fast(Ff * r) / (Ff * __sinf(x));
 }
 
 // Uniform dispatch between the accurate and the fast forms.

@@ -1139,6 +1139,29 @@ int psf_clean(psf_plan_t p, const psf_clean_t *cfg, float *residual, float *mode
     return run_clean(p, cfg, residual, model, comp_pix, comp_flux, niter_out, (cudaStream_t)stream);
 }
 
+int psf_fwhm(psf_plan_t p, const psf_batch_t *b, const float *cutouts_dev, double *fwhm_dev, void *stream) {
+    if (!p || !cutouts_dev || !fwhm_dev) return PSF_EINVAL;
+    BatchHost h;
+    int s = prepare_batch(p, b, h, 4096);
+    if (s) return s;
+    if (h.npos == 0) return PSF_OK;
+    std::vector<FwhmItem> items((size_t)h.npos);
+    for (int i = 0; i < h.npos; ++i) {
+        const double l0 = b->lm[2 * i], m0 = b->lm[2 * i + 1], rho = std::sqrt(l0 * l0 + m0 * m0);
+        if (h.npix[i] < 4) return PSF_EINVAL;
+        items[i].er_x = rho > 0 ? (float)(l0 / rho) : 1.f;
+        items[i].er_y = rho > 0 ? (float)(m0 / rho) : 0.f;
+        items[i].N = h.npix[i];
+        items[i].pad = 0;
+        items[i].off = h.out_off[i];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((s = upload_meta(p, items.data(), items.size() * sizeof(FwhmItem), st))) return s;
+    PSF_TRY(launch_fwhm(cutouts_dev, (const FwhmItem *)p->meta.p, h.npos, h.cell, fwhm_dev, st));
+    if (p->prof) p->n_kernels++;
+    return PSF_OK;
+}
+
 int psf_img_grid_table(psf_plan_t p, int npix, double cell_rad, float *table_dev, void *stream) {
     if (!p || !table_dev || !(cell_rad > 0.0)) return PSF_EINVAL;
     if (!img_grid_supported(npix)) return PSF_EUNSUPPORTED;

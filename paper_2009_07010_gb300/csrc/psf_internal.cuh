@@ -167,4 +167,13 @@ cudaError_t launch_clean_prep(const unsigned long long *key, unsigned long long 
 cudaError_t launch_clean_sub(float *res, float *model, const float *P, CleanState *st, int nl, int nm, int N,
                              float gain, int32_t *comp_pix, float *comp_flux, cudaStream_t s);
 
+// ---- FWHM along radial / tangential directions (k_fwhm.cu) --------------------
+struct FwhmItem {
+    float er_x, er_y;   // radial unit vector in pixel axes (l, m); the l axis at l0 = 0
+    int32_t N;          // cutout size
+    int32_t pad;
+    long long off;      // float offset of the cutout
+};
+cudaError_t launch_fwhm(const float *cut, const FwhmItem *items, int npos, double cell, double *out, cudaStream_t s);
+
 }  // namespace psf
