@@ -407,6 +407,61 @@ def measure_clean(psf, plan, nl=2048, nsrc=200, npix=128, gain=0.1, iters=None):
             "speedup_over_exact_per_iteration": {m: ref / v["ms_per_iteration"] for m, v in out.items()}}
 
 
+def measure_facets(psf, plan, nl=2048, nsrc=200, npix=128, gain=0.1, iters=3000):
+    """Position-dependent PSFs against one PSF per facet (the faceting approach of
+    Sect. 3.3, Eqs. 57-58) on the benchmark observation.  CLEAN: an nl x nl image at 1.5"
+    centred 2 deg from the phase centre, nsrc seeded sources shaped like the gridded PSF at
+    their pixels; cleaned with the PSF at each peak and with the one PSF at the image
+    centre; residual max / rms over the brightest source after `iters` iterations, and time
+    per iteration.  PSF cost: 16 facet-centre exact PSFs of 256^2 pixels against nsrc
+    per-source exact PSFs of 128^2 and nsrc per-source gridded PSFs."""
+    import torch
+    rng = np.random.default_rng(obsgen.SEED_BASE + 8)
+    cell, N = obsgen.config2_batch().cell_rad, npix
+    centre = (float(np.sin(np.radians(2.0))), 0.0)
+    xs = rng.integers(N // 2, nl - N // 2, nsrc)
+    ys = rng.integers(N // 2, nl - N // 2, nsrc)
+    fl = np.minimum(rng.uniform(0.0, 1.0, nsrc) ** -1.5, 100.0)
+    lm = np.stack([centre[0] + (xs - nl // 2) * cell, centre[1] + (ys - nl // 2) * cell], axis=1)
+    P = plan.approx_img_grid(psf.Batch(lm, N, cell)).view(nsrc, N, N)
+    P = P / P[:, N // 2, N // 2].view(nsrc, 1, 1)
+    dirty = torch.zeros((nl, nl), dtype=torch.float32, device="cuda")
+    for k in range(nsrc):
+        dirty[ys[k] - N // 2:ys[k] + N // 2, xs[k] - N // 2:xs[k] + N // 2] += float(fl[k]) * P[k]
+    out = {}
+    for name, facet in (("position_dependent", False), ("facet_psf", True)):
+        r = dirty.clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, _, cp, _ = plan.clean(r, cell, N, method="img_grid", gain=gain, threshold=0.0, max_iter=iters,
+                                 centre=centre, facet_psf=facet)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        out[name] = {"iterations": int(len(cp)), "ms_per_iteration": dt * 1e3 / max(1, len(cp)),
+                     "residual_max_over_brightest": float(r.abs().max()) / float(fl.max()),
+                     "residual_rms_over_brightest": float(r.pow(2).mean().sqrt()) / float(fl.max())}
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - t0) * 1e3
+    fl_lm = []
+    for a in range(4):
+        for b in range(4):
+            fl_lm.append((centre[0] + (a - 1.5) * nl / 4 * cell, centre[1] + (b - 1.5) * nl / 4 * cell))
+    fb = psf.Batch(np.array(fl_lm), 256, cell)
+    sb = psf.Batch(lm, N, cell)
+    cost = {"facet_exact_16x256px_ms": timed(lambda: plan.exact(fb)),
+            "per_source_exact_ms": timed(lambda: plan.exact(sb)),
+            "per_source_img_grid_ms": timed(lambda: plan.approx_img_grid(sb))}
+    if plan.sync_status() != 0:
+        raise RuntimeError("device-side error in the facet measurement")
+    return {"workload": f"meerkat64_4h_16ch_facet_{nl}px_at_2deg_{nsrc}src", "clean_gridded_psf": out,
+            "psf_cost": cost}
+
+
 def measure_fwhm(psf, prec):
     """PSF size against distance from the phase centre as in the paper's FWHM figure: the
     64-antenna array at 1.4 GHz, 2 h of 1 s samples, 6 MHz of 50 kHz channels averaged
@@ -503,9 +558,10 @@ def main():
     ap.add_argument("--no-grid", action="store_true")
     ap.add_argument("--no-clean", action="store_true")
     ap.add_argument("--no-fwhm", action="store_true")
+    ap.add_argument("--no-facets", action="store_true")
     ap.add_argument("--grid-positions", type=int, default=16384,
                     help="positions of the gridded-form measurement (radial grid out to 3 deg)")
-    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean", "facets"],
                     help="c2: the 4 h MeerKAT-shaped cutout; c2_1h: the same array and cutout over 1 h "
                          "(a quarter of the visibilities, for profiler captures); c4: only the batched "
                          "256 x 64^2 measurement (profiler captures of the batched kernel); grid: only "
@@ -529,6 +585,15 @@ def main():
         torch.cuda.set_device(local)
         with psf.Plan(obsgen.config2_obs(), prec=args.prec) as plan:
             res = measure_clean(psf, plan)
+        print(json.dumps(res), flush=True)
+        return 0
+    if args.workload == "facets":
+        import torch
+        import paper_2009_07010_gb300 as psf
+        psf.build_library()
+        torch.cuda.set_device(local)
+        with psf.Plan(obsgen.config2_obs(), prec=args.prec) as plan:
+            res = measure_facets(psf, plan)
         print(json.dumps(res), flush=True)
         return 0
     if args.workload == "grid":
@@ -651,6 +716,7 @@ def main():
                                                                        npos=args.grid_positions)
     clean = None if args.no_clean or rank != 0 else measure_clean(psf, plan)
     fwhm = None if args.no_fwhm or rank != 0 else measure_fwhm(psf, args.prec)
+    facets = None if args.no_facets or rank != 0 else measure_facets(psf, plan)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
@@ -680,7 +746,7 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

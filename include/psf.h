@@ -216,8 +216,14 @@ typedef struct {
     float gain;            /* CLEAN gain gamma, 0 < gain <= 1 */
     float threshold;       /* stop once the peak residual is <= threshold */
     int32_t max_iter;      /* >= 0 */
-    int32_t reserved;
+    int32_t options;       /* PSF_CLEAN_* bits */
 } psf_clean_t;
+
+/* One PSF for the whole image: the cutout at the image centre (l_c, m_c), computed once
+ * and used for every component -- the faceting approach the paper's cost comparison
+ * considers (Sect. 3.3, Eqs. 57-58: the PSF at each facet's centre), instead of the PSF
+ * at each peak. */
+#define PSF_CLEAN_FACET_PSF 1u
 
 /* Runs the loop of psf_clean_t on the device and returns when it has stopped (the
  * stream is synchronized).  residual_dev: device float32 [nm][nl], in: the dirty image,
@@ -227,7 +233,8 @@ typedef struct {
  * flux gain * I_D(l0).  *niter_out (host, may be NULL): iterations performed.  With
  * PSF_METHOD_IMG_GRID every step stays on the device and the host reads the loop
  * record once per 64 queued iterations; the other methods read the peak record back
- * each iteration to place the cutout.  Errors: PSF_EINVAL (sizes, gain, method, NULL
+ * each iteration to place the cutout (with PSF_CLEAN_FACET_PSF every method stays on
+ * the device after the one PSF evaluation).  Errors: PSF_EINVAL (sizes, gain, method, NULL
  * residual), PSF_EUNSUPPORTED (a cutout size the method does not support,
  * PSF_COMPLEX_OUT), and those of the PSF calls. */
 int psf_clean(psf_plan_t plan, const psf_clean_t *cfg, float *residual_dev, float *model_dev,

@@ -221,7 +221,7 @@ def psf_img_grid_from_tables(tables, lm, npix: int, cell: float, flags: int = 0)
 
 
 def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: float, max_iter: int,
-          flags: int = 0, margins: bool = False, centre=(0.0, 0.0), follow=None):
+          flags: int = 0, margins: bool = False, centre=(0.0, 0.0), follow=None, facet_psf: bool = False):
     """Hogbom CLEAN with position-dependent PSFs (Algorithm 2), float64.
 
     dirty [nm, nl]: the dirty image; pixel (x, y) is the direction (l_c + (x - nl/2) cell,
@@ -238,7 +238,8 @@ def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: fl
     threshold test; the fourth return value is then [(max I_D, I_D at the pixel taken), ...]
     per iteration, so that another implementation's choices can be checked against this
     one's values (where two pixels are within rounding of each other, either is a correct
-    argmax)."""
+    argmax).  With facet_psf, the PSF at the image centre `centre` serves every component
+    (the faceting approach of Sect. 3.3, Eqs. 57-58) instead of the PSF at each peak."""
     res = np.array(dirty, np.float64, copy=True)
     nm, nl = res.shape
     model = np.zeros_like(res)
@@ -246,6 +247,7 @@ def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: fl
     N = int(npix)
     mid = {"exact": EXACT, "uv": UV, "img": IMG}
     tables = grid_tables(obs, N, cell) if method == "img_grid" else None
+    Pfix = None
     niter = int(max_iter) if follow is None else len(follow)
     for it in range(niter):
         if follow is None:
@@ -262,17 +264,24 @@ def clean(obs, method, dirty, cell: float, npix: int, gain: float, threshold: fl
             gaps.append(peak - float(np.max(res)))
             res[y, x] = peak
         l0, m0 = centre[0] + (x - nl // 2) * cell, centre[1] + (y - nm // 2) * cell
-        if method == "img_grid":
-            P = psf_img_grid_from_tables(tables, [[l0, m0]], N, cell, flags=flags)[0]
+        if facet_psf:
+            l0, m0 = centre
+        if facet_psf and Pfix is not None:
+            P = Pfix
         else:
-            class _B:
-                pass
-            b = _B()
-            b.lm = np.array([[l0, m0]])
-            b.npix = np.array([N], np.int32)
-            b.cell_rad = cell
-            P = psf(obs, mid[method], b, flags=flags).reshape(N, N)
-        P = P / P[N // 2, N // 2]
+            if method == "img_grid":
+                P = psf_img_grid_from_tables(tables, [[l0, m0]], N, cell, flags=flags)[0]
+            else:
+                class _B:
+                    pass
+                b = _B()
+                b.lm = np.array([[l0, m0]])
+                b.npix = np.array([N], np.int32)
+                b.cell_rad = cell
+                P = psf(obs, mid[method], b, flags=flags).reshape(N, N)
+            P = P / P[N // 2, N // 2]
+            if facet_psf:
+                Pfix = P
         g = gain * peak
         y0, x0 = y - N // 2, x - N // 2
         ya, yb = max(y0, 0), min(y0 + N, nm)

@@ -14,6 +14,7 @@ from . import build as _build
 PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_EUNSUPPORTED, PSF_ETIMEOUT = 0, -1, -2, -3, -4, -5
 PSF_FP32, PSF_TC_FP16, PSF_TC_BF16 = 0, 1, 3
 PSF_WTERM, PSF_IMG_LITERAL_THETA, PSF_DETERMINISTIC, PSF_COMPLEX_OUT = 1, 2, 4, 8
+PSF_CLEAN_FACET_PSF = 1
 PSF_ALGO_AUTO, PSF_ALGO_CUTOUT = 0, 1
 EXACT, UV, IMG, IMG_GRID = 0, 1, 2, 3
 
@@ -26,7 +27,7 @@ EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_nvis", "psf_exact", "psf_a
 class CleanT(ctypes.Structure):
     _fields_ = [("nl", ctypes.c_int32), ("nm", ctypes.c_int32), ("cell_rad", ctypes.c_double),
                 ("l_c", ctypes.c_double), ("m_c", ctypes.c_double), ("psf_npix", ctypes.c_int32), ("method", ctypes.c_int32), ("gain", ctypes.c_float),
-                ("threshold", ctypes.c_float), ("max_iter", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("threshold", ctypes.c_float), ("max_iter", ctypes.c_int32), ("options", ctypes.c_int32)]
 
 
 class PsfError(RuntimeError):

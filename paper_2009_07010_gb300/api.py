@@ -134,10 +134,11 @@ class Plan:
 
     def clean(self, dirty: torch.Tensor, cell: float, npix: int, method: str = "img_grid", gain: float = 0.1,
               threshold: float = 0.0, max_iter: int = 1000, model: Optional[torch.Tensor] = None,
-              centre=(0.0, 0.0), stream=None):
+              centre=(0.0, 0.0), facet_psf: bool = False, stream=None):
         """Hogbom CLEAN with position-dependent PSFs (Algorithm 2) on the device.  dirty:
         float32 CUDA tensor [nm, nl], overwritten with the residual; pixel (nl/2, nm/2) looks
-        at `centre` (l, m).  Returns (residual,
+        at `centre` (l, m).  facet_psf: one PSF at `centre` for every component (faceting)
+        instead of the PSF at each peak.  Returns (residual,
         model, component pixel indices [niter], component fluxes [niter])."""
         assert dirty.dtype == torch.float32 and dirty.is_cuda and dirty.is_contiguous() and dirty.dim() == 2
         nm, nl = dirty.shape
@@ -147,7 +148,7 @@ class Plan:
         cflux = torch.empty(max(max_iter, 1), dtype=torch.float32, device=dirty.device)
         mcode = {"exact": _lib.EXACT, "uv": _lib.UV, "img": _lib.IMG, "img_grid": _lib.IMG_GRID}[method]
         cfg = _lib.CleanT(nl, nm, float(cell), float(centre[0]), float(centre[1]), int(npix), mcode, float(gain),
-                          float(threshold), int(max_iter), 0)
+                          float(threshold), int(max_iter), _lib.PSF_CLEAN_FACET_PSF if facet_psf else 0)
         n = ctypes.c_int32(0)
         check(_lib.lib().psf_clean(self._h, ctypes.byref(cfg), ctypes.c_void_p(dirty.data_ptr()),
                                    ctypes.c_void_p(model.data_ptr()), ctypes.c_void_p(cpix.data_ptr()),

@@ -1064,6 +1064,8 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
     if ((int64_t)c->nl * c->nm >= (int64_t(1) << 31)) return PSF_EUNSUPPORTED;
     if (p->opts.flags & PSF_COMPLEX_OUT) return PSF_EUNSUPPORTED;
     if (c->method == PSF_METHOD_IMG_GRID && !img_grid_supported(N)) return PSF_EUNSUPPORTED;
+    if (c->options & ~PSF_CLEAN_FACET_PSF) return PSF_EINVAL;
+    const bool facet = (c->options & PSF_CLEAN_FACET_PSF) != 0;
     if (niter_out) *niter_out = 0;
     if (c->max_iter == 0) return PSF_OK;
     const size_t ws_bytes = sizeof(CleanState) + 2 * sizeof(unsigned long long);
@@ -1077,7 +1079,32 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
     const int64_t npx = (int64_t)c->nl * c->nm;
     CleanState h{};
     int64_t t = 0;
-    if (c->method == PSF_METHOD_IMG_GRID) {
+    if (facet) {
+        // the PSF at the image centre, once; then every iteration stays on the device
+        double lm[2] = {c->l_c, c->m_c};
+        psf_batch_t b{};
+        b.npos = 1;
+        b.lm = lm;
+        b.npix0 = N;
+        b.cell_rad = c->cell_rad;
+        int s = c->method == PSF_METHOD_IMG_GRID ? run_img_grid(p, &b, (float *)P.p, st)
+                                                 : run_forward(p, c->method, &b, (float *)P.p, st);
+        if (s) return s;
+        constexpr int kChunk = 64;
+        for (;;) {
+            for (int q = 0; q < kChunk; ++q, ++t) {
+                PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
+                PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
+                                          c->l_c, c->m_c, c->threshold, c->max_iter, literal, st));
+                PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
+                                         st));
+            }
+            if (p->prof) p->n_kernels += 3 * kChunk;
+            PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
+            PSF_TRY(cudaStreamSynchronize(st));
+            if (h.done) break;
+        }
+    } else if (c->method == PSF_METHOD_IMG_GRID) {
         const float4 *G = nullptr;
         int s = grid_tables(p, N, c->cell_rad, st, &G);
         if (s) return s;

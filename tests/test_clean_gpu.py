@@ -52,7 +52,7 @@ def _device_psf(psf, plan, method, l0, m0, N, cell):
     return P / P[N // 2, N // 2]
 
 
-def _run(psf, obs, plan, method, nl, nm, cell, centre, N, srcs, gain, thr, maxit):
+def _run(psf, obs, plan, method, nl, nm, cell, centre, N, srcs, gain, thr, maxit, facet_psf=False):
     import torch
     dg, do = np.zeros((nm, nl)), np.zeros((nm, nl))
     for x, y, c in srcs:
@@ -61,11 +61,12 @@ def _run(psf, obs, plan, method, nl, nm, cell, centre, N, srcs, gain, thr, maxit
         _place(do, _oracle_psf(obs, method, l0, m0, N, cell), x, y, c)
     dirty = torch.tensor(dg, dtype=torch.float32, device="cuda")
     res, model, cpix, cflux = plan.clean(dirty, cell, N, method=method, gain=gain, threshold=thr, max_iter=maxit,
-                                         centre=centre)
+                                         centre=centre, facet_psf=facet_psf)
     assert plan.sync_status() == 0
     cpix, cflux = cpix.cpu().numpy(), cflux.cpu().numpy().astype(np.float64)
     res, model = res.cpu().numpy().astype(np.float64), model.cpu().numpy().astype(np.float64)
-    ro, mo, comps, trace = oracle.clean(obs, method, do, cell, N, gain, thr, maxit, centre=centre, follow=cpix)
+    ro, mo, comps, trace = oracle.clean(obs, method, do, cell, N, gain, thr, maxit, centre=centre, follow=cpix,
+                                        facet_psf=facet_psf)
     scale = max(c for _, _, c in srcs)
     for k, (mx, val) in enumerate(trace):
         assert mx - val <= TOL * scale, (k, mx, val)
@@ -87,6 +88,17 @@ def test_clean_overlapping_sources(psf, method):
     with psf.Plan(obs, prec="fp32") as plan:
         n = _run(psf, obs, plan, method, 96, 96, 2 * ARC, (0.02, 0.02), 32,
                  [(40, 50, 1.0), (52, 44, 0.8), (30, 35, 0.65)], 0.25, 0.15, 60)
+    assert n > 10
+
+
+@pytest.mark.parametrize("method", ["exact", "img_grid"])
+def test_clean_facet_psf(psf, method):
+    """One PSF at the image centre for every component (faceting): the same sources as
+    above, so the subtracted shape differs from each source's own PSF."""
+    obs = obsgen.config1_obs()
+    with psf.Plan(obs, prec="fp32") as plan:
+        n = _run(psf, obs, plan, method, 96, 96, 2 * ARC, (0.02, 0.02), 32,
+                 [(40, 50, 1.0), (52, 44, 0.8), (30, 35, 0.65)], 0.25, 0.15, 60, facet_psf=True)
     assert n > 10
 
 

@@ -108,3 +108,39 @@ def test_c5_window_clipped_at_the_image_edge():
     ref = np.zeros_like(d)
     _place(ref, P, x, y, c * 0.125)
     np.testing.assert_allclose(res, ref, rtol=0, atol=1e-12)
+
+
+def test_c6_facet_psf_closed_form():
+    """One PSF at the image centre for every component (faceting, Eqs. 57-58): a source at
+    the centre pixel is cleaned exactly as with position-dependent PSFs; an off-centre
+    source, taken at its own pixel every time, leaves c P_src - c (1 - (1-gain)^K) P_centre
+    (the centre PSF, not its own, is subtracted)."""
+    obs = obsgen.tiny_obs(weights=True)
+    centre = (0.01, 0.005)          # the normalised PSF peaks at its centre pixel here
+    gain, thr = 0.3, 0.1
+    xc, yc = NL // 2, NM // 2
+    def psf_at(x, y):
+        l0, m0 = centre[0] + (x - NL // 2) * CELL, centre[1] + (y - NM // 2) * CELL
+        b = obsgen.Batch(np.array([[l0, m0]]), np.array([N], np.int32), CELL)
+        P = oracle.psf(obs, oracle.UV, b).reshape(N, N)
+        return P / P[N // 2, N // 2]
+    Pc = psf_at(xc, yc)
+    d = np.zeros((NM, NL))
+    _place(d, Pc, xc, yc, 1.0)
+    a = oracle.clean(obs, "uv", d, CELL, N, gain, thr, 100, centre=centre)
+    b = oracle.clean(obs, "uv", d, CELL, N, gain, thr, 100, centre=centre, facet_psf=True)
+    np.testing.assert_allclose(a[0], b[0], rtol=0, atol=1e-12)
+    assert [i for i, _ in a[2]] == [i for i, _ in b[2]]
+    x, y = xc + 9, yc - 6
+    Ps = psf_at(x, y)
+    d = np.zeros((NM, NL))
+    _place(d, Ps, x, y, 1.0)
+    res, model, comps = oracle.clean(obs, "uv", d, CELL, N, gain, thr, 100, centre=centre, facet_psf=True)
+    K = len(comps)
+    assert all(i == y * NL + x for i, _ in comps)
+    np.testing.assert_allclose([g for _, g in comps], gain * (1 - gain) ** np.arange(K), rtol=1e-12)
+    ref = np.zeros_like(d)
+    _place(ref, Ps, x, y, 1.0)
+    _place(ref, Pc, x, y, -(1 - (1 - gain) ** K))
+    np.testing.assert_allclose(res, ref, rtol=0, atol=1e-12)
+    assert np.max(np.abs(Ps - Pc)) > 1e-3          # the two PSFs do differ
