@@ -232,7 +232,8 @@ typedef struct {
  * [max_iter] or NULL: per iteration the peak pixel index y * nl + x and the subtracted
  * flux gain * I_D(l0).  *niter_out (host, may be NULL): iterations performed.  With
  * PSF_METHOD_IMG_GRID every step stays on the device and the host reads the loop
- * record once per 64 queued iterations; the other methods read the peak record back
+ * record once per 64 queued iterations (after the first 64, replayed as one CUDA graph
+ * on a private stream); the other methods read the peak record back
  * each iteration to place the cutout (with PSF_CLEAN_FACET_PSF every method stays on
  * the device after the one PSF evaluation).  Errors: PSF_EINVAL (sizes, gain, method, NULL
  * residual), PSF_EUNSUPPORTED (a cutout size the method does not support,

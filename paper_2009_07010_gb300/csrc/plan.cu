@@ -1079,49 +1079,77 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
     const int64_t npx = (int64_t)c->nl * c->nm;
     CleanState h{};
     int64_t t = 0;
-    if (facet) {
-        // the PSF at the image centre, once; then every iteration stays on the device
-        double lm[2] = {c->l_c, c->m_c};
-        psf_batch_t b{};
-        b.npos = 1;
-        b.lm = lm;
-        b.npix0 = N;
-        b.cell_rad = c->cell_rad;
-        int s = c->method == PSF_METHOD_IMG_GRID ? run_img_grid(p, &b, (float *)P.p, st)
-                                                 : run_forward(p, c->method, &b, (float *)P.p, st);
-        if (s) return s;
-        constexpr int kChunk = 64;
-        for (;;) {
-            for (int q = 0; q < kChunk; ++q, ++t) {
-                PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
-                PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
-                                          c->l_c, c->m_c, c->threshold, c->max_iter, literal, st));
-                PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
-                                         st));
-            }
-            if (p->prof) p->n_kernels += 3 * kChunk;
-            PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
-            PSF_TRY(cudaStreamSynchronize(st));
-            if (h.done) break;
-        }
-    } else if (c->method == PSF_METHOD_IMG_GRID) {
+    if (facet || c->method == PSF_METHOD_IMG_GRID) {
+        // every step of an iteration on the device: the PSF at the image centre once
+        // (facet), or the gridded PSF at each peak from the kept table
         const float4 *G = nullptr;
-        int s = grid_tables(p, N, c->cell_rad, st, &G);
-        if (s) return s;
+        if (facet) {
+            double lm[2] = {c->l_c, c->m_c};
+            psf_batch_t b{};
+            b.npos = 1;
+            b.lm = lm;
+            b.npix0 = N;
+            b.cell_rad = c->cell_rad;
+            int s = c->method == PSF_METHOD_IMG_GRID ? run_img_grid(p, &b, (float *)P.p, st)
+                                                     : run_forward(p, c->method, &b, (float *)P.p, st);
+            if (s) return s;
+        } else {
+            int s = grid_tables(p, N, c->cell_rad, st, &G);
+            if (s) return s;
+        }
+        // one chunk of kChunk iterations; kChunk is even, so the alternating argmax keys
+        // repeat identically in every chunk
         constexpr int kChunk = 64;
-        for (;;) {
-            for (int q = 0; q < kChunk; ++q, ++t) {
-                PSF_TRY(launch_clean_argmax(res, npx, sd, key + (t & 1), p->nsm, st));
-                PSF_TRY(launch_clean_prep(key + (t & 1), key + ((t + 1) & 1), sd, c->nl, c->nm, c->cell_rad,
-                                          c->l_c, c->m_c, c->threshold, c->max_iter, literal, st));
-                PSF_TRY(launch_img_grid(G, &sd->gpos, 1, N, (float *)P.p, p->nsm, st));
-                PSF_TRY(launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
-                                         st));
+        const int per_iter = facet ? 3 : 4;
+        auto chunk = [&](cudaStream_t cs) -> cudaError_t {
+            for (int q = 0; q < kChunk; ++q) {
+                cudaError_t e = launch_clean_argmax(res, npx, sd, key + (q & 1), p->nsm, cs);
+                if (e == cudaSuccess)
+                    e = launch_clean_prep(key + (q & 1), key + ((q + 1) & 1), sd, c->nl, c->nm, c->cell_rad, c->l_c,
+                                          c->m_c, c->threshold, c->max_iter, literal, cs);
+                if (e == cudaSuccess && !facet) e = launch_img_grid(G, &sd->gpos, 1, N, (float *)P.p, p->nsm, cs);
+                if (e == cudaSuccess)
+                    e = launch_clean_sub(res, model, (const float *)P.p, sd, c->nl, c->nm, N, c->gain, cpix, cflux,
+                                         cs);
+                if (e != cudaSuccess) return e;
             }
-            if (p->prof) p->n_kernels += 4 * kChunk;
-            PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
-            PSF_TRY(cudaStreamSynchronize(st));
-            if (h.done) break;
+            return cudaSuccess;
+        };
+        // the first chunk on the caller's stream (it also sets the kernels' one-time
+        // attributes); the loop record is read once per chunk
+        PSF_TRY(chunk(st));
+        if (p->prof) p->n_kernels += per_iter * kChunk;
+        PSF_TRY(cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, st));
+        PSF_TRY(cudaStreamSynchronize(st));
+        if (!h.done) {
+            // later chunks: the same launches captured once into a CUDA graph and replayed on
+            // a private stream (the caller's stream has drained; the call returns after the
+            // private stream does)
+            cudaStream_t cs = nullptr;
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ge = nullptr;
+            cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+            if (e == cudaSuccess) {
+                const cudaError_t ec = chunk(cs);
+                e = cudaStreamEndCapture(cs, &g);
+                if (ec != cudaSuccess) e = ec;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+            while (e == cudaSuccess) {
+                e = cudaGraphLaunch(ge, cs);
+                if (e == cudaSuccess) e = cudaMemcpyAsync(&h, sd, sizeof(h), cudaMemcpyDeviceToHost, cs);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(cs);
+                if (p->prof) p->n_kernels += per_iter * kChunk;
+                if (e == cudaSuccess && h.done) break;
+            }
+            if (ge) cudaGraphExecDestroy(ge);
+            if (g) cudaGraphDestroy(g);
+            if (cs) cudaStreamDestroy(cs);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return cuda_status(e);
+            }
         }
     } else {
         double lm[2] = {0.0, 0.0};
