@@ -42,6 +42,8 @@ class Observation:
     favg: int                    # raw channels per averaged channel
     weights: Optional[np.ndarray] = None   # float32 [nvis] in plan order, or None
     enu_m: Optional[np.ndarray] = None     # antenna positions (for reference only)
+    time_window: Optional[np.ndarray] = None   # float32 [sum(tavg)]: per baseline, over a bin's samples
+    chan_window: Optional[np.ndarray] = None   # float32 [nbl, favg]: per baseline, over an output channel's raw channels
 
     @property
     def nbl(self) -> int:
@@ -226,6 +228,25 @@ def fig3_batch(npix: int = 64, cell_arcsec: float = 1.0, radii_deg=(0.0, 0.5, 1.
             lm.append((s * math.cos(phi), s * math.sin(phi)))
     lm = np.array(lm)
     return Batch(lm, np.full(len(lm), npix, np.int32), cell_arcsec * ARCSEC)
+
+
+def bd_windows(obs: Observation, strength: float = 1.0):
+    """Seeded-free example of baseline-dependent windows (input data for the windowed
+    average): per baseline a Gaussian taper over the tavg[b] samples of a bin and over the
+    favg raw channels of an output channel, narrower on longer baselines (sigma = n /
+    (1 + strength |b| / b_median) samples), as baseline-dependent windows are.  Returns
+    (time_window [sum(tavg)], chan_window [nbl, favg]) as float32."""
+    blen = np.linalg.norm(obs.uvw_m.mean(axis=1), axis=1)
+    med = max(float(np.median(blen)), 1e-9)
+    tw, cw = [], np.empty((obs.nbl, obs.favg), np.float32)
+    for b in range(obs.nbl):
+        scale = 1.0 + strength * blen[b] / med
+        n = int(obs.tavg[b])
+        k = np.arange(n) - 0.5 * (n - 1)
+        tw.append(np.exp(-0.5 * (k / (n / scale)) ** 2))
+        f = np.arange(obs.favg) - 0.5 * (obs.favg - 1)
+        cw[b] = np.exp(-0.5 * (f / (max(obs.favg, 1) / scale)) ** 2)
+    return np.concatenate(tw).astype(np.float32), cw
 
 
 def tiny_obs(seed: int = 7, nant: int = 4, ntime: int = 24, nchan: int = 4,

@@ -54,7 +54,7 @@ def _load():
         if _lib is None:
             lib = ctypes.CDLL(build())
             P = ctypes.c_void_p
-            obs_args = [ctypes.c_int] * 4 + [P] * 6
+            obs_args = [ctypes.c_int] * 4 + [P] * 8
             lib.or_nvis.restype = ctypes.c_int64
             lib.or_nvis.argtypes = [ctypes.c_int] * 4 + [P]
             lib.or_vis_table.restype = ctypes.c_int
@@ -94,12 +94,15 @@ class _Obs:
         self.w = np.ascontiguousarray(obs.chan_width_hz, np.float64)
         self.tavg = np.ascontiguousarray(obs.tavg, np.int32)
         self.wt = None if obs.weights is None else np.ascontiguousarray(obs.weights, np.float32)
+        tw, cw = getattr(obs, "time_window", None), getattr(obs, "chan_window", None)
+        self.tw = None if tw is None else np.ascontiguousarray(tw, np.float32)
+        self.cw = None if cw is None else np.ascontiguousarray(cw, np.float32)
         self.nbl, self.ntime = self.uvw.shape[0], self.uvw.shape[1]
         self.nchan, self.favg = self.f.shape[0], int(obs.favg)
 
     def args(self):
         return [self.nbl, self.ntime, self.nchan, self.favg, _p(self.uvw), _p(self.t),
-                _p(self.f), _p(self.w), _p(self.tavg), _p(self.wt)]
+                _p(self.f), _p(self.w), _p(self.tavg), _p(self.wt), _p(self.tw), _p(self.cw)]
 
 
 def nvis(obs) -> int:

@@ -52,11 +52,14 @@ typedef struct {
     const double *width;   /* [nchan] */
     const int *tavg;       /* [nbl] */
     const float *weights;  /* [nvis] or NULL */
+    const float *twin;     /* time windows: per baseline tavg[b] values, concatenated, or NULL */
+    const float *cwin;     /* channel windows: [nbl][favg], or NULL */
 } or_obs;
 
 /* Per averaged visibility k, everything the definitions need. */
 typedef struct {
     int b, s0, n, r;       /* baseline, first raw sample, sample count, out channel */
+    int64_t toff;          /* offset of the baseline's time window in or_obs.twin */
     double ubar[3];        /* bin-mean uvw [m] (Eq. 12 bin centre) */
     double dedge[3];       /* uvw(t_e) - uvw(t_s) [m] (Eq. 33 edges) */
     double nu, dnu, dt;    /* nu_r, Delta nu_r, Delta t_k */
@@ -105,7 +108,8 @@ static or_vis *or_make_vis(const or_obs *o, int64_t *nvis_out) {
     or_vis *v = (or_vis *)calloc((size_t)nvis, sizeof(or_vis));
     double dt = or_dt(o);
     int64_t k = 0;
-    for (int b = 0; b < o->nbl; ++b) {
+    int64_t toff = 0;
+    for (int b = 0; b < o->nbl; toff += o->tavg[b], ++b) {
         int n = o->tavg[b];
         int nbins = o->ntime / n;
         const double *ub = o->uvw + (size_t)b * o->ntime * 3;
@@ -126,7 +130,7 @@ static or_vis *or_make_vis(const or_obs *o, int64_t *nvis_out) {
             }
             for (int r = 0; r < nout; ++r, ++k) {
                 or_vis *x = &v[k];
-                x->b = b; x->s0 = s0; x->n = n; x->r = r;
+                x->b = b; x->s0 = s0; x->n = n; x->r = r; x->toff = toff;
                 double nu = 0, dnu = 0;
                 for (int c = r * o->favg; c < (r + 1) * o->favg; ++c) {
                     nu += o->freq[c];
@@ -202,11 +206,23 @@ static void or_decorr_one(const or_obs *o, const or_vis *x, int method, double l
         const double *ub = o->uvw + (size_t)x->b * o->ntime * 3;
         double Xbar = or_dot3(x->ubar, L);
         double Xbar_l = or_dot3(x->ubar, dLl), Xbar_m = or_dot3(x->ubar, dLm);
+        /* windowed average (Eqs. 15-16): time weight per raw sample of the bin and
+         * channel weight per raw channel, each normalised to sum 1 (a channel's weight
+         * is its window value times its width); the boxcar is 1/n and dnu_c / Dnu_r */
+        double tnorm = 0, cnorm = 0;
+        if (o->twin)
+            for (int s = 0; s < x->n; ++s) tnorm += o->twin[x->toff + s];
+        if (o->cwin)
+            for (int c = x->r * o->favg; c < (x->r + 1) * o->favg; ++c)
+                cnorm += (double)o->cwin[(int64_t)x->b * o->favg + (c - x->r * o->favg)] * o->width[c];
         for (int s = x->s0; s < x->s0 + x->n; ++s) {
             const double *us = ub + s * 3;
             double Xs = or_dot3(us, L), Xs_l = or_dot3(us, dLl), Xs_m = or_dot3(us, dLm);
+            const double ft = o->twin ? o->twin[x->toff + (s - x->s0)] / tnorm : 1.0 / x->n;
             for (int c = x->r * o->favg; c < (x->r + 1) * o->favg; ++c) {
-                double f = o->width[c] / (x->dnu * x->n);
+                const double fc = o->cwin ? o->cwin[(int64_t)x->b * o->favg + (c - x->r * o->favg)] * o->width[c] / cnorm
+                                          : o->width[c] / x->dnu;
+                double f = ft * fc;
                 double phi = (o->freq[c] * Xs - x->nu * Xbar) / OR_C_LIGHT;
                 double y = Xs * o->width[c] / OR_C_LIGHT;
                 double S = or_sincpi(y), dS = or_dsincpi(y) * o->width[c] / OR_C_LIGHT;
@@ -241,8 +257,9 @@ static void or_decorr_one(const or_obs *o, const or_vis *x, int method, double l
 }
 
 #define OR_OBS_ARGS int nbl, int ntime, int nchan, int favg, const double *uvw, const double *time_s, \
-    const double *freq, const double *width, const int *tavg, const float *weights
-#define OR_OBS_INIT {nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights}
+    const double *freq, const double *width, const int *tavg, const float *weights, const float *twin, \
+    const float *cwin
+#define OR_OBS_INIT {nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights, twin, cwin}
 
 /* Per-visibility table: u,v,w [lambda] at nu_r, nu_r, Dnu_r, Dt_k, W_k, bin-mean uvw [m],
  * bin-edge delta [m].  Row layout: 13 doubles. */
@@ -540,8 +557,8 @@ int or_psf_img_grid(OR_OBS_ARGS, int npos, const double *lm, int N, double cell,
     const int64_t NN = (int64_t)N * N;
     double *S = (double *)malloc(sizeof(double) * 2 * NN);
     double *dtc = (double *)malloc(sizeof(double) * NN), *rc = (double *)malloc(sizeof(double) * NN);
-    int rc0 = or_grid_tables(nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights, N, cell,
-                             S, dtc, rc, NULL, NULL);
+    int rc0 = or_grid_tables(nbl, ntime, nchan, favg, uvw, time_s, freq, width, tavg, weights, twin, cwin, N,
+                             cell, S, dtc, rc, NULL, NULL);
     if (rc0 == 0) rc0 = or_psf_img_grid_tables(N, cell, S, dtc, rc, npos, lm, flags, out);
     free(S); free(dtc); free(rc);
     return rc0;
