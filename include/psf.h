@@ -143,6 +143,22 @@ typedef struct {
  * and must be released with psf_plan_destroy. */
 int psf_plan(const psf_obs_t *obs, const psf_opts_t *opts, psf_plan_t *out);
 
+/* Windowed averaging (Sect. 2.3, Eqs. 15-16): the normalised boxcar over a bin's raw
+ * samples and an output channel's raw channels replaced by a window X_pqkr, for the
+ * exact method (psf_exact, the batched form and psf_adjoint; Methods 1 and 2 keep their
+ * boxcar models).  Host float32 arrays, read during the call, either may be NULL (boxcar
+ * in that direction; both NULL restores the boxcar):
+ *   time_window  per baseline b the tavg[b] weights of a bin's raw samples, in bin order,
+ *                concatenated over the baselines (sum of tavg entries)
+ *   chan_window  [nbl][favg]: per baseline the weights of an output channel's favg raw
+ *                channels
+ * Each baseline's windows are normalised by the library: the time weights to sum 1, and
+ * per output channel the products weight x raw-channel width to sum 1 (so a constant
+ * window is the boxcar).  The windows cover each bin's own samples (bins stay disjoint).
+ * PSF_EINVAL for a negative or non-finite weight or a window that sums to 0;
+ * PSF_ENOMEM / PSF_ECUDA on allocation or copy failure. */
+int psf_plan_set_windows(psf_plan_t plan, const float *time_window, const float *chan_window);
+
 /* Replace the precision / flags / algorithm used by later calls on this plan. */
 int psf_plan_set_opts(psf_plan_t plan, const psf_opts_t *opts);
 

@@ -88,6 +88,19 @@ class Plan:
         self._keep = None
         self.prec, self.flags, self.algo = prec, flags, algo
         self.nvis = int(L.psf_plan_nvis(h))
+        tw, cw = getattr(obs, "time_window", None), getattr(obs, "chan_window", None)
+        if tw is not None or cw is not None:
+            self.set_windows(tw, cw)
+
+    def set_windows(self, time_window=None, chan_window=None):
+        """Windowed averaging of the exact method (Eqs. 15-16): per-baseline weights over a
+        bin's raw samples (concatenated over baselines) and [nbl, favg] over an output
+        channel's raw channels; None for the boxcar."""
+        tw = None if time_window is None else np.ascontiguousarray(time_window, np.float32)
+        cw = None if chan_window is None else np.ascontiguousarray(chan_window, np.float32)
+        check(_lib.lib().psf_plan_set_windows(self._h, None if tw is None else ctypes.c_void_p(tw.ctypes.data),
+                                              None if cw is None else ctypes.c_void_p(cw.ctypes.data)),
+              "psf_plan_set_windows")
 
     def set_opts(self, prec: Optional[str] = None, flags: Optional[int] = None, algo: Optional[int] = None):
         self.prec = prec if prec is not None else self.prec

@@ -116,7 +116,9 @@ __device__ __forceinline__ void sincospi2_t(float x, float *s, float *c) {   // 
 
 // Exact bin average (Eq. 13), centre phase removed.  With uniform channels the
 // channel sum is the Dirichlet kernel times the per-channel sinc (exact identity
-// for equally spaced, equally wide channels); otherwise channels are summed.
+// for equally spaced, equally wide channels); otherwise channels are summed.  With
+// windows (Eqs. 15-16) each raw sample carries its normalised time weight and each raw
+// channel its normalised channel weight in place of 1/n and dnu_c / Dnu_r.
 // grad (optional): d/dl0 (re, im), d/dm0 (re, im) with dL0/dl0 = dLl, dL0/dm0 = dLm.
 template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, float4 L, float4 dLl,
@@ -128,8 +130,11 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
     float re = 0.f, im = 0.f, glr = 0.f, gli = 0.f, gmr = 0.f, gmi = 0.f;
     float Xbl = 0.f, Xbm = 0.f;
     if (GRAD) { Xbl = dot3(ub, dLl); Xbm = dot3(ub, dLm); }
+    const bool win = o.win != 0;
+    const float *cw = win ? o.chan_win + (int64_t)o.bin_bl[bin] * (o.nout * o.favg) + (int64_t)r * o.favg : nullptr;
     for (int s = 0; s < sm.y; ++s) {
         const float4 d = o.samp[sm.x + s];
+        const float wt = win ? o.samp_w[sm.x + s] : 1.0f;
         const float ds = dot3(d, L);
         const float Xs = Xbar + ds;
         // exp(-2 pi i nu_r ds / c): the sample's offset from the bin centre
@@ -137,7 +142,7 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
         sincospi2_t<FAST>(-ch.x * ds * kInvC, &sn, &cs);
         float dsl = 0.f, dsm = 0.f;
         if (GRAD) { dsl = dot3(d, dLl); dsm = dot3(d, dLm); }
-        if (o.uniform) {
+        if (o.uniform && !win) {
             const float a = ch.z * Xs * kInvC;
             const float y = ch.w * Xs * kInvC;
             const float dir = dirichlet_t<FAST>(o.favg, a);
@@ -162,12 +167,13 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
                 float s2, c2;
                 sincospi2_t<FAST>(-rc.x * Xs * kInvC, &s2, &c2);
                 const float y = rc.y * Xs * kInvC;
-                const float S = sincpi_t<FAST>(y) * rc.z;
+                const float cwt = win ? wt * cw[c] : rc.z;
+                const float S = sincpi_t<FAST>(y) * cwt;
                 const float er = cs * c2 - sn * s2, ei = cs * s2 + sn * c2;
                 re += er * S;
                 im += ei * S;
                 if (GRAD) {
-                    const float dS = dsincpi(y) * rc.y * kInvC * rc.z;
+                    const float dS = dsincpi(y) * rc.y * kInvC * cwt;
                     const float Xl = Xbl + dsl, Xm = Xbm + dsm;
                     const float pl = -2.0f * kPiF * (ch.x * dsl + rc.x * Xl) * kInvC;
                     const float pm = -2.0f * kPiF * (ch.x * dsm + rc.x * Xm) * kInvC;
@@ -179,7 +185,7 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
             }
         }
     }
-    const float inv = 1.0f / (float)sm.y;
+    const float inv = win ? 1.0f : 1.0f / (float)sm.y;
     if (GRAD) *grad = make_float4(glr * inv, gli * inv, gmr * inv, gmi * inv);
     return make_float2(re * inv, im * inv);
 }

@@ -101,6 +101,12 @@ struct psf_plan_s {
     // first bin: the nearest-cell decisions of the gridded image-plane form
     DevBuf bin_uv64, chan64, bin_first;
     double dt_raw = 0;
+    // windowed average (Eqs. 15-16): host copies of the binning, device tables
+    std::vector<int32_t> h_tavg;
+    std::vector<double> h_width;
+    std::vector<int64_t> h_bin_first, h_samp_first;
+    int affine0 = 0;
+    DevBuf samp_w, chan_win, bin_bl;
     // gridded image-plane tables, one per (cutout size, pixel size, precision)
     struct Grid {
         int N = 0;
@@ -303,6 +309,14 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     UP(bin_first, h_bf)
 #undef UP
     p->dt_raw = dt;
+    try {
+        p->h_tavg.assign(o->tavg, o->tavg + o->nbl);
+        p->h_width.assign(o->chan_width_hz, o->chan_width_hz + o->nchan);
+        p->h_bin_first = bin_first;
+        p->h_samp_first = samp_first;
+    } catch (...) {
+        return fail(PSF_ENOMEM);
+    }
     if (e == cudaSuccess) e = p->W.reserve(nvis * sizeof(float));
     // uv is padded with zeros to a whole number of 32-visibility stages plus one
     // stage, so bulk copies of full stages never leave the buffer
@@ -336,6 +350,7 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     }
     DevObs &d = p->d;
     d.chan_affine = affine;
+    p->affine0 = affine;
     d.dnu_ch = (float)dnu_ch;
     d.nvis = (int32_t)nvis; d.nbin = (int32_t)nbin; d.nout = nout; d.favg = o->favg; d.uniform = uniform;
     d.dt = (float)dt;
@@ -351,6 +366,69 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_status(e)); }
     *out = p;
+    return PSF_OK;
+}
+
+int psf_plan_set_windows(psf_plan_t p, const float *tw, const float *cw) {
+    if (!p) return PSF_EINVAL;
+    DevObs &d = p->d;
+    if (!tw && !cw) {   // back to the boxcar
+        d.win = 0;
+        d.chan_affine = p->affine0;
+        return PSF_OK;
+    }
+    const int nbl = p->nbl, favg = p->favg, nout = p->nout, nchan = p->nchan;
+    std::vector<float> h_sw, h_cw;
+    std::vector<int32_t> h_bl;
+    try {
+        h_sw.resize((size_t)p->nsamp);
+        h_cw.resize((size_t)nbl * nchan);
+        h_bl.resize((size_t)p->nbin);
+    } catch (...) {
+        return PSF_ENOMEM;
+    }
+    int64_t toff = 0;
+    for (int b = 0; b < nbl; ++b) {
+        const int n = p->h_tavg[b];
+        double sum = 0;
+        for (int s = 0; s < n; ++s) {
+            const double v = tw ? (double)tw[toff + s] : 1.0;
+            if (!std::isfinite(v) || v < 0) return PSF_EINVAL;
+            sum += v;
+        }
+        if (!(sum > 0)) return PSF_EINVAL;
+        const int64_t nb = p->h_bin_first[b + 1] - p->h_bin_first[b];
+        for (int64_t tau = 0; tau < nb; ++tau) {
+            const int64_t rec = p->h_samp_first[b] + tau * n;
+            for (int s = 0; s < n; ++s) h_sw[rec + s] = (float)((tw ? (double)tw[toff + s] : 1.0) / sum);
+            h_bl[p->h_bin_first[b] + tau] = b;
+        }
+        toff += n;
+        for (int r = 0; r < nout; ++r) {
+            double cs = 0;
+            for (int j = 0; j < favg; ++j) {
+                const double v = cw ? (double)cw[(int64_t)b * favg + j] : 1.0;
+                if (!std::isfinite(v) || v < 0) return PSF_EINVAL;
+                cs += v * p->h_width[r * favg + j];
+            }
+            if (!(cs > 0)) return PSF_EINVAL;
+            for (int j = 0; j < favg; ++j) {
+                const double v = cw ? (double)cw[(int64_t)b * favg + j] : 1.0;
+                h_cw[(int64_t)b * nchan + r * favg + j] = (float)(v * p->h_width[r * favg + j] / cs);
+            }
+        }
+    }
+    PSF_TRY(p->samp_w.reserve(std::max<size_t>(16, h_sw.size() * sizeof(float))));
+    PSF_TRY(p->chan_win.reserve(std::max<size_t>(16, h_cw.size() * sizeof(float))));
+    PSF_TRY(p->bin_bl.reserve(std::max<size_t>(16, h_bl.size() * sizeof(int32_t))));
+    PSF_TRY(cudaMemcpy(p->samp_w.p, h_sw.data(), h_sw.size() * sizeof(float), cudaMemcpyHostToDevice));
+    PSF_TRY(cudaMemcpy(p->chan_win.p, h_cw.data(), h_cw.size() * sizeof(float), cudaMemcpyHostToDevice));
+    PSF_TRY(cudaMemcpy(p->bin_bl.p, h_bl.data(), h_bl.size() * sizeof(int32_t), cudaMemcpyHostToDevice));
+    d.samp_w = (const float *)p->samp_w.p;
+    d.chan_win = (const float *)p->chan_win.p;
+    d.bin_bl = (const int32_t *)p->bin_bl.p;
+    d.win = 1;
+    d.chan_affine = 0;   // the channel recurrence of the exact weights assumes the boxcar
     return PSF_OK;
 }
 

@@ -31,6 +31,11 @@ struct DevObs {
     const float4 *rawchan;    // [nout*favg] nu_c - nu_r, dnu_c, dnu_c / Dnu_r, 0
     const float *W;           // [nvis] visibility weights
     const float2 *uv;         // [nvis] bin-centre (u, v) in wavelengths
+    // windowed average (Eqs. 15-16), exact method; win = 0: the boxcar
+    int32_t win;
+    const float *samp_w;      // [nsamp] normalised time weight of each raw-sample record
+    const float *chan_win;    // [nbl][nchan] normalised channel weight (window x width)
+    const int32_t *bin_bl;    // [nbin] baseline of each bin
 };
 
 // One cutout tile of a contraction launch.

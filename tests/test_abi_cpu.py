@@ -51,6 +51,7 @@ def test_null_handles(L):
     assert L.psf_clean(None, ctypes.byref(cfg), None, None, None, None, None, None) == _lib.PSF_EINVAL
     assert ctypes.sizeof(_lib.CleanT) == 56
     assert L.psf_fwhm(None, ctypes.byref(b), None, None, None) == _lib.PSF_EINVAL
+    assert L.psf_plan_set_windows(None, None, None) == _lib.PSF_EINVAL
     assert L.psf_approx_uv_img(None, ctypes.byref(b), None, None, None) == _lib.PSF_EINVAL
     assert L.psf_adjoint(None, 0, ctypes.byref(b), None, None, None, None) == _lib.PSF_EINVAL
     assert L.psf_sync_status(None, None) == _lib.PSF_EINVAL
