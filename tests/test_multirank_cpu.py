@@ -69,3 +69,62 @@ def test_two_ranks_reassemble_single_process_result():
     got = np.concatenate([p[1] for p in sorted(parts, key=lambda x: x[0])])
     assert got.shape == ref.shape
     np.testing.assert_array_equal(got, ref)
+
+
+# ---- CLEAN by facets: each facet image is cleaned on its own, so facets shard like positions
+
+def _facets():
+    """Four 48 x 48 facets of a field centred on (0.01, 0.005), one source each, on the
+    small array; the facet-centre PSF serves every component of a facet."""
+    obs = obsgen.tiny_obs(weights=True)
+    cell, N, nf = 3e-5, 16, 48
+    centres = [(0.01 + dx * nf * cell, 0.005 + dy * nf * cell) for dy in (-0.5, 0.5) for dx in (-0.5, 0.5)]
+    srcs = [(20, 22, 1.0), (27, 25, 0.8), (24, 19, 0.9), (22, 26, 0.7)]
+    return obs, cell, N, nf, centres, srcs
+
+
+def _clean_facet(f):
+    import oracle
+    obs, cell, N, nf, centres, srcs = _facets()
+    x, y, c = srcs[f]
+    l0, m0 = centres[f][0] + (x - nf // 2) * cell, centres[f][1] + (y - nf // 2) * cell
+    b = obsgen.Batch(np.array([[l0, m0]]), np.array([N], np.int32), cell)
+    P = oracle.psf(obs, oracle.UV, b).reshape(N, N)
+    d = np.zeros((nf, nf))
+    d[y - N // 2:y + N // 2, x - N // 2:x + N // 2] = c * P / P[N // 2, N // 2]
+    res, model, comps = oracle.clean(obs, "uv", d, cell, N, 0.3, 0.1, 50, centre=centres[f], facet_psf=True)
+    return res, comps
+
+
+def _facet_worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    a, b = shard.shard_ranges(np.full(4, 48), world)[rank]
+    mine = [(f, _clean_facet(f)) for f in range(a, b)]
+    parts = [None] * world
+    dist.all_gather_object(parts, mine)
+    if rank == 0:
+        q.put(parts)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_clean_facets_like_one_process():
+    world = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_facet_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    parts = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    got = dict(item for part in parts for item in part)
+    assert sorted(got) == [0, 1, 2, 3]
+    for f in range(4):
+        res, comps = _clean_facet(f)
+        np.testing.assert_array_equal(got[f][0], res)
+        assert got[f][1] == comps and len(comps) > 1
