@@ -299,19 +299,19 @@ int psf_profile_read(psf_plan_t plan, double *contraction_ms, int64_t *contracti
 
 /* Exact smeared PSF of ONE cutout without allocating device memory during the call.
  * No counterpart in the paper: it exists for callers that cannot allocate while they
- * compute -- code inside a CUDA stream capture (cudaMalloc cannot be captured),
- * real-time or embedded pipelines that forbid allocation after start-up, plug-ins
- * whose host application's allocator owns the device memory.  It reads the plan's
- * arrays (allocated earlier by psf_plan) and writes npix*npix floats to out_dev
- * (device, row j = m offset, column i = l offset, as psf_exact); the computation is
- * the FP32 path with the weights evaluated inline.
+ * compute -- real-time or embedded pipelines that forbid allocation once they have
+ * started, and plug-ins whose host application's allocator owns the device memory.
+ * It reads the plan's arrays (allocated earlier by psf_plan) and writes npix*npix
+ * floats to out_dev (device, row j = m offset, column i = l offset, as psf_exact); the
+ * computation is the FP32 path with the weights evaluated inline.
  * Scratch: a fixed 16 MiB array inside the library's device image (every GPU that
  * loads the library holds it until the process exits); it keeps the last call's
  * contents, nothing in it needs to start at zero, and calls that overlap on the GPU
  * (e.g. on two streams) race on it.  The first call on each device looks up the
  * array's device address (cudaGetSymbolAddress); make that first call before any
- * stream capture.  Limits: npix even, 2 <= npix <= 256 (PSF_EUNSUPPORTED beyond);
- * l0^2 + m0^2 < 1, cell_rad > 0 (PSF_EINVAL otherwise).  Calls no allocating routine. */
+ * stream capture.  The current device must be the plan's (PSF_EINVAL otherwise).
+ * Limits: npix even, 2 <= npix <= 256 (PSF_EUNSUPPORTED beyond); l0^2 + m0^2 < 1,
+ * cell_rad > 0 (PSF_EINVAL otherwise).  Calls no allocating routine. */
 int psf_exact_noalloc(psf_plan_t plan, double l0, double m0, int npix, double cell_rad, float *out_dev,
                       void *cuda_stream);
 

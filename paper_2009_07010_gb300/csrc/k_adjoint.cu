@@ -11,12 +11,13 @@
 // A CTA owns a contiguous range of visibilities; each thread owns kAdjT of them.
 // For every position and every 32-row block of R (staged transposed in shared
 // memory) a thread forms t_j = sum_i R[j][i] a_k[i] for the 32 rows (row twiddles by
-// complex recurrence, re-seeded from sincospif every 32 columns), then adds
+// complex recurrence, re-seeded every 32 columns from float-float phases), then adds
 // sum_j b_k[j] t_j into H.  After the last block D_k and its gradient are evaluated
 // (decorr<true>) and folded into dL/dW_k (registers; written once per call, no
 // atomics) and into per-thread position sums, which are reduced over the block and
 // written to a per-CTA partial buffer; a second kernel adds the partials in float64.
 #include "decorr.cuh"
+#include "fp32_tile.cuh"
 
 namespace psf {
 namespace {
@@ -30,12 +31,6 @@ __device__ __forceinline__ float2 acmul(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__device__ __forceinline__ float2 cis_turns_acc(float x) {
-    float s, c;
-    sincospif(2.0f * x, &s, &c);
-    return make_float2(c, s);
-}
-
 struct AdjPos {
     float4 L, dLl, dLm;   // direction (l0, m0, n0-1) and its derivatives
 };
@@ -43,7 +38,7 @@ struct AdjPos {
 __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevObs o, int method, uint32_t flags,
                                                          const AdjPos *__restrict__ pos,
                                                          const int32_t *__restrict__ npix,
-                                                         const int64_t *__restrict__ offs, int npos, float cell,
+                                                         const int64_t *__restrict__ offs, int npos, float2 cell,
                                                          const float *__restrict__ R, float *__restrict__ gW,
                                                          int accumulate_gW, double *__restrict__ partial) {
     extern __shared__ __align__(16) float RT[];   // [N][kAdjRows], transposed block of R
@@ -76,14 +71,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevObs o, int method, u
             for (int t = 0; t < kAdjT; ++t) {
                 const int32_t k = kk[t];
                 if (k >= o.nvis) continue;
-                const float2 uvk = o.uv[k];
-                const float tu = uvk.x * cell, tv = uvk.y * cell;
-                const float2 zu = cis_turns_acc(tu);
+                // pixel phases per unit offset as float-float pairs (fp32_tile.cuh): seeds
+                // and steps lose their whole turns exactly before rounding
+                const float2 uh = o.uv[k], ul = o.uv_lo[k];
+                const float2 tu = fp32t::ff_mul(uh.x, ul.x, cell.x, cell.y);
+                const float2 tv = fp32t::ff_mul(uh.y, ul.y, cell.x, cell.y);
+                const float2 zu = fp32t::cis_acc(fp32t::ff_turns(tu, 1));
                 float tre[kAdjRows], tim[kAdjRows];
 #pragma unroll
                 for (int jj = 0; jj < kAdjRows; ++jj) { tre[jj] = 0.f; tim[jj] = 0.f; }
                 for (int i0 = 0; i0 < N; i0 += 32) {
-                    float2 a = cis_turns_acc(tu * (float)(i0 - half));
+                    float2 a = fp32t::cis_acc(fp32t::ff_turns(tu, i0 - half));
                     const int iend = min(N, i0 + 32);
                     for (int i = i0; i < iend; ++i) {
                         const float4 *row = reinterpret_cast<const float4 *>(RT + i * kAdjRows);
@@ -102,8 +100,8 @@ __global__ void __launch_bounds__(kAdjThreads) k_adjoint(DevObs o, int method, u
                         a = acmul(a, zu);
                     }
                 }
-                float2 b = cis_turns_acc(tv * (float)(j0 - half));
-                const float2 zv = cis_turns_acc(tv);
+                float2 b = fp32t::cis_acc(fp32t::ff_turns(tv, j0 - half));
+                const float2 zv = fp32t::cis_acc(fp32t::ff_turns(tv, 1));
                 float2 h = H[t];
 #pragma unroll
                 for (int jj = 0; jj < kAdjRows; ++jj) {
@@ -170,7 +168,7 @@ int adjoint_max_n() { return kAdjMaxN; }
 int64_t adjoint_ctas(int64_t nvis) { return (nvis + kAdjThreads * kAdjT - 1) / (kAdjThreads * kAdjT); }
 
 cudaError_t launch_adjoint_chunk(const DevObs &o, int method, uint32_t flags, const void *pos, const int32_t *npix,
-                                 const int64_t *offs, int npos, int nmax, float cell, const float *R, float *gW,
+                                 const int64_t *offs, int npos, int nmax, double cell, const float *R, float *gW,
                                  int accumulate_gW, double *partial, double *g_lm, cudaStream_t st) {
     if (npos <= 0) return cudaSuccess;
     const int64_t ncta = adjoint_ctas(o.nvis);
@@ -178,7 +176,7 @@ cudaError_t launch_adjoint_chunk(const DevObs &o, int method, uint32_t flags, co
     cudaError_t e = cudaFuncSetAttribute(k_adjoint, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k_adjoint<<<(unsigned)ncta, kAdjThreads, smem, st>>>(o, method, flags, (const AdjPos *)pos, npix, offs, npos,
-                                                         cell, R, gW, accumulate_gW, partial);
+                                                         fp32t::cell_pair(cell), R, gW, accumulate_gW, partial);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_adjoint_reduce<<<(npos * 2 + 255) / 256, 256, 0, st>>>(partial, (int)ncta, npos, g_lm);

@@ -5,19 +5,17 @@
 // visibilities with coalesced 16-byte loads of the bin records.
 //
 // FP32 contraction (Eqs. 21-22 as a separable DFT): a CTA owns a 64 x 64 pixel tile
-// of one cutout and a contiguous range of visibilities.  Per chunk of 32
-// visibilities it stages the row twiddles a_k[i] = exp(2 pi i u_k dl_i) and the
-// weighted column twiddles c_k[j] = w_k exp(2 pi i v_k dm_j) in shared memory
-// (generated by complex recurrence from sincospif seeds), then every thread
-// accumulates a 4 x 4 pixel block of Re(c a) with two FMAs per term.  Sums are
-// kept short in FP32 (one chunk) and folded into a compensated (Kahan) FP32 total,
-// and split-K partials are added in float64, so the path meets 1e-6 relative.
+// of one cutout and a contiguous range of visibilities; the tile body (twiddle chains
+// from float-float seed phases, 4 x 4 pixel blocks per thread, compensated FP32 sums)
+// is fp32t::tile_sum, and split-K partials are added in float64, so the path meets
+// 1e-6 relative.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <algorithm>
 
 #include "decorr.cuh"
+#include "fp32_tile.cuh"
 
 namespace psf {
 
@@ -321,104 +319,34 @@ cudaError_t launch_zero_cutouts(float *out, const int64_t *offs, const int32_t *
 }
 
 // --------------------------------------------------------------- FP32 contraction
-namespace {
-constexpr int kT = 64;    // tile edge (pixels)
-constexpr int kKC = 32;   // visibilities per shared-memory chunk
-constexpr int kSeg = 16;  // twiddles per recurrence chain
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-}  // namespace
-
-__global__ void __launch_bounds__(256) k_psf_fp32(const float2 *__restrict__ uv,
-                                                  const float2 *__restrict__ w, int64_t ldw,
-                                                  int32_t nvis, const Tile *__restrict__ tiles,
-                                                  int32_t kper, float cell, float *__restrict__ partial,
-                                                  int64_t split_stride) {
-    __shared__ __align__(16) float2 sa[kKC][kT];   // row (l) twiddles
-    __shared__ __align__(16) float2 sc[kKC][kT];   // weighted column (m) twiddles
+// One CTA per (64 x 64 tile, visibility range); the tile body is fp32t::tile_sum.
+__global__ void __launch_bounds__(256) k_psf_fp32(const float2 *__restrict__ uv, const float2 *__restrict__ uv_lo,
+                                                  const float2 *__restrict__ w, int64_t ldw, int32_t nvis,
+                                                  const Tile *__restrict__ tiles, int32_t kper, float2 cell,
+                                                  float *__restrict__ partial, int64_t split_stride) {
+    __shared__ __align__(16) float2 sa[fp32t::kKC][fp32t::kT];   // row (l) twiddles
+    __shared__ __align__(16) float2 sc[fp32t::kKC][fp32t::kT];   // weighted column (m) twiddles
     const Tile t = tiles[blockIdx.x];
     const int split = blockIdx.y;
     const int32_t kbeg = split * kper;
     const int32_t kend = min(nvis, kbeg + kper);
     const float2 *wp = w + (int64_t)t.slot * ldw;
-    const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
-    // generator role: visibility lane gk of the chunk, 16-twiddle segment gs (0-3 rows, 4-7 cols)
-    const int gk = tid & 31, gs = tid >> 5;
-    const int half = t.N / 2;
-    const int seg_first = (gs & 3) * kSeg;
-    const int n_first = (gs < 4 ? t.i0 : t.j0) + seg_first - half;   // pixel offset index of the chain start
-
-    float acc[4][4], tot[4][4], cmp[4][4];
+    float tot[4][4];
 #pragma unroll
     for (int b = 0; b < 4; ++b)
 #pragma unroll
-        for (int a = 0; a < 4; ++a) { acc[b][a] = 0.f; tot[b][a] = 0.f; cmp[b][a] = 0.f; }
-
-    for (int32_t kc = kbeg; kc < kend; kc += kKC) {
-        const int32_t k = kc + gk;
-        float2 seed = make_float2(0.f, 0.f), step = make_float2(1.f, 0.f);
-        if (k < kend) {
-            const float2 uvk = uv[k];
-            const float theta = (gs < 4 ? uvk.x : uvk.y) * cell;   // turns per pixel
-            sincospif(2.0f * theta * (float)n_first, &seed.y, &seed.x);
-            sincospif(2.0f * theta, &step.y, &step.x);
-            if (gs >= 4) seed = cmul(seed, wp[k]);
-        }
-        __syncthreads();   // previous chunk consumed
-        float2 *dst = (gs < 4 ? &sa[gk][seg_first] : &sc[gk][seg_first]);
-#pragma unroll
-        for (int q = 0; q < kSeg; ++q) {
-            dst[q] = seed;
-            seed = cmul(seed, step);
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kKC; ++kk) {
-            const float4 a01 = *reinterpret_cast<const float4 *>(&sa[kk][tx * 4]);
-            const float4 a23 = *reinterpret_cast<const float4 *>(&sa[kk][tx * 4 + 2]);
-            const float4 c01 = *reinterpret_cast<const float4 *>(&sc[kk][ty * 4]);
-            const float4 c23 = *reinterpret_cast<const float4 *>(&sc[kk][ty * 4 + 2]);
-            const float ar[4] = {a01.x, a01.z, a23.x, a23.z}, ai[4] = {a01.y, a01.w, a23.y, a23.w};
-            const float cr[4] = {c01.x, c01.z, c23.x, c23.z}, ci[4] = {c01.y, c01.w, c23.y, c23.w};
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-#pragma unroll
-                for (int a = 0; a < 4; ++a) acc[b][a] = fmaf(cr[b], ar[a], fmaf(-ci[b], ai[a], acc[b][a]));
-        }
-        // fold the chunk sum into the compensated total
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const float y = acc[b][a] - cmp[b][a];
-                const float s = tot[b][a] + y;
-                cmp[b][a] = (s - tot[b][a]) - y;
-                tot[b][a] = s;
-                acc[b][a] = 0.f;
-            }
-    }
-    float *dst = partial + (int64_t)split * split_stride + t.out_off;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-        const int j = t.j0 + ty * 4 + b;
-        if (j >= t.N) continue;
-#pragma unroll
-        for (int a = 0; a < 4; ++a) {
-            const int i = t.i0 + tx * 4 + a;
-            if (i < t.N) dst[(int64_t)j * t.N + i] = tot[b][a];
-        }
-    }
+        for (int a = 0; a < 4; ++a) tot[b][a] = 0.f;
+    fp32t::tile_sum(uv, uv_lo, kbeg, kend, t.N, t.i0, t.j0, cell, [&](int32_t k) { return wp[k]; }, sa, sc, tot);
+    fp32t::tile_store(partial + (int64_t)split * split_stride + t.out_off, t.N, t.i0, t.j0, tot);
 }
 
 cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles, int ntiles,
-                            int nsplit, int32_t kper, float cell, float *partial, int64_t split_stride,
+                            int nsplit, int32_t kper, double cell, float *partial, int64_t split_stride,
                             cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
     dim3 grid(ntiles, nsplit);
-    k_psf_fp32<<<grid, 256, 0, st>>>(o.uv, w, ldw, o.nvis, tiles, kper, cell, partial, split_stride);
+    k_psf_fp32<<<grid, 256, 0, st>>>(o.uv, o.uv_lo, w, ldw, o.nvis, tiles, kper, fp32t::cell_pair(cell), partial,
+                                     split_stride);
     return cudaGetLastError();
 }
 
@@ -455,21 +383,28 @@ cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, cons
 }
 
 // --------------------------------------------------------------- per-visibility tables
-// uv[k] = ubar (x, y) nu_r / c in wavelengths; W[k] = tavg * favg when no weights given.
-__global__ void __launch_bounds__(256) k_fill_vis(DevObs o, float2 *__restrict__ uv, float *__restrict__ W,
-                                                  int natural) {
+// uv[k] + uv_lo[k] = ubar (x, y) nu_r / c in wavelengths, formed in float64 from the bin
+// means and channel frequencies and split into a rounded float pair; W[k] = tavg * favg
+// when no weights are given.
+__global__ void __launch_bounds__(256) k_fill_vis(DevObs o, const double2 *__restrict__ bin_uv64,
+                                                  const double2 *__restrict__ chan64, float2 *__restrict__ uv,
+                                                  float2 *__restrict__ uv_lo, float *__restrict__ W, int natural) {
     const int32_t k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= o.nvis) return;
     const int bin = k / o.nout;
     const int r = k - bin * o.nout;
-    const float4 ub = o.bin_ubar[bin];
-    const float s = o.chan[r].x * kInvC;
-    uv[k] = make_float2(ub.x * s, ub.y * s);
+    const double2 ub = bin_uv64[bin];
+    const double nu = chan64[r].x;
+    const double u = ub.x * nu / kCLight, v = ub.y * nu / kCLight;
+    const float uh = (float)u, vh = (float)v;
+    uv[k] = make_float2(uh, vh);
+    uv_lo[k] = make_float2((float)(u - (double)uh), (float)(v - (double)vh));
     if (natural) W[k] = (float)(o.bin_samp[bin].y * o.favg);
 }
 
-cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st) {
-    k_fill_vis<<<(o.nvis + 255) / 256, 256, 0, st>>>(o, uv, W, natural);
+cudaError_t launch_fill_vis(const DevObs &o, const double2 *bin_uv64, const double2 *chan64, float2 *uv,
+                            float2 *uv_lo, float *W, int natural, cudaStream_t st) {
+    k_fill_vis<<<(o.nvis + 255) / 256, 256, 0, st>>>(o, bin_uv64, chan64, uv, uv_lo, W, natural);
     return cudaGetLastError();
 }
 

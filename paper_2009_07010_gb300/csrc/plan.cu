@@ -96,7 +96,7 @@ struct psf_plan_s {
     int64_t nbin = 0, nsamp = 0, nvis = 0;
     DevObs d{};
     // position-independent device arrays
-    DevBuf bin_ubar, bin_edge, bin_samp, samp, chan, rawchan, W, uv;
+    DevBuf bin_ubar, bin_edge, bin_samp, samp, chan, rawchan, W, uv, uv_lo;
     // float64 bin-mean (u, v) [m], output channels (nu_r, Dnu_r) and each baseline's
     // first bin: the nearest-cell decisions of the gridded image-plane form
     DevBuf bin_uv64, chan64, bin_first;
@@ -322,6 +322,8 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     // stage, so bulk copies of full stages never leave the buffer
     if (e == cudaSuccess) e = p->uv.reserve((size_t)(nvis + 64) * sizeof(float2));
     if (e == cudaSuccess) e = cudaMemset(p->uv.p, 0, (size_t)(nvis + 64) * sizeof(float2));
+    if (e == cudaSuccess) e = p->uv_lo.reserve((size_t)(nvis + 64) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMemset(p->uv_lo.p, 0, (size_t)(nvis + 64) * sizeof(float2));
     if (e == cudaSuccess) e = p->err.reserve(sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->err.p, 0, sizeof(int));
     if (e == cudaSuccess && o->weights)
@@ -362,7 +364,9 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
     d.rawchan = (const float4 *)p->rawchan.p;
     d.W = (const float *)p->W.p;
     d.uv = (const float2 *)p->uv.p;
-    e = launch_fill_vis(d, (float2 *)p->uv.p, (float *)p->W.p, o->weights ? 0 : 1, 0);
+    d.uv_lo = (const float2 *)p->uv_lo.p;
+    e = launch_fill_vis(d, (const double2 *)p->bin_uv64.p, (const double2 *)p->chan64.p, (float2 *)p->uv.p,
+                        (float2 *)p->uv_lo.p, (float *)p->W.p, o->weights ? 0 : 1, 0);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) { cudaGetLastError(); return fail(cuda_status(e)); }
     *out = p;
@@ -798,7 +802,7 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
         }
         if (!tc) {
             PSF_TRY(launch_psf_fp32(p->d, w, ldw, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
-                                    kper, (float)h.cell, part, stride, st));
+                                    kper, h.cell, part, stride, st));
         } else {
             int wreal = method != PSF_METHOD_EXACT ? 1 : 0;
             if (wreal) {
@@ -1364,7 +1368,7 @@ int psf_adjoint(psf_plan_t p, int method, const psf_batch_t *b, const float *dLd
         char *dm = (char *)p->meta.p;
         PSF_TRY(p->partial.reserve((size_t)ncta * cn * 2 * sizeof(double)));
         PSF_TRY(launch_adjoint_chunk(p->d, method, p->opts.flags, dm + off_pos, (const int32_t *)(dm + off_npix),
-                                     (const int64_t *)(dm + off_offs), cn, nmax, (float)h.cell, dLdP, dLdW,
+                                     (const int64_t *)(dm + off_offs), cn, nmax, h.cell, dLdP, dLdW,
                                      c0 > 0, (double *)p->partial.p, dLdlm + 2 * c0, st));
         p->n_kernels += 2;
     }
@@ -1401,6 +1405,7 @@ int psf_profile_read(psf_plan_t p, double *ms, int64_t *ncontract, int64_t *nker
 namespace psf {
 const DevObs *plan_devobs(psf_plan_t p) { return p ? &p->d : nullptr; }
 uint32_t plan_flags(psf_plan_t p) { return p ? p->opts.flags : 0u; }
+int plan_device(psf_plan_t p) { return p ? p->device : -1; }
 }  // namespace psf
 
 extern "C" {

@@ -30,7 +30,8 @@ struct DevObs {
     const float4 *chan;       // [nout] nu_r, Dnu_r, channel spacing, channel width
     const float4 *rawchan;    // [nout*favg] nu_c - nu_r, dnu_c, dnu_c / Dnu_r, 0
     const float *W;           // [nvis] visibility weights
-    const float2 *uv;         // [nvis] bin-centre (u, v) in wavelengths
+    const float2 *uv;         // [nvis] bin-centre (u, v) in wavelengths, rounded to float32
+    const float2 *uv_lo;      // [nvis] (u, v) - uv: the float64 bin centre is uv + uv_lo
     // windowed average (Eqs. 15-16), exact method; win = 0: the boxcar
     int32_t win;
     const float *samp_w;      // [nsamp] normalised time weight of each raw-sample record
@@ -59,21 +60,23 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
                            cudaStream_t st);
 // FP32 CUDA-core contraction; partial[split * split_stride + out_off + j*N + i].
 cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const Tile *tiles,
-                            int ntiles, int nsplit, int32_t kper, float cell, float *partial,
+                            int ntiles, int nsplit, int32_t kper, double cell, float *partial,
                             int64_t split_stride, cudaStream_t st);
 // out[out_off_p + q] = sum_s partial[s * stride + loc_off_p + q'] (float64 sum), where
 // q' = q for row-major partials and q' = i N + j for q = j N + i when `transposed`.
 cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, const int64_t *loc_offs,
                           const int64_t *out_offs, const int32_t *npix, int npos, int transposed, float *out,
                           cudaStream_t st);
-// Plan-time per-visibility tables: uv[k] and, if natural, W[k] = tavg * favg.
-cudaError_t launch_fill_vis(const DevObs &o, float2 *uv, float *W, int natural, cudaStream_t st);
+// Plan-time per-visibility tables: uv[k] + uv_lo[k] (from the float64 bin means and
+// channel frequencies) and, if natural, W[k] = tavg * favg.
+cudaError_t launch_fill_vis(const DevObs &o, const double2 *bin_uv64, const double2 *chan64, float2 *uv,
+                            float2 *uv_lo, float *W, int natural, cudaStream_t st);
 // Adjoint (vector-Jacobian product) in FP32, see psf_adjoint (k_adjoint.cu).
 // pos: [npos] {L, dL/dl0, dL/dm0} float4 triples; partial: [ctas][npos][2] doubles.
 int adjoint_max_n();
 int64_t adjoint_ctas(int64_t nvis);
 cudaError_t launch_adjoint_chunk(const DevObs &o, int method, uint32_t flags, const void *pos, const int32_t *npix,
-                                 const int64_t *offs, int npos, int nmax, float cell, const float *R, float *gW,
+                                 const int64_t *offs, int npos, int nmax, double cell, const float *R, float *gW,
                                  int accumulate_gW, double *partial, double *g_lm, cudaStream_t st);
 
 // ---- tcgen05 contraction (k_tc.cu) ----------------------------------------
@@ -131,6 +134,7 @@ cudaError_t launch_zero_cutouts(float *out, const int64_t *offs, const int32_t *
 // Read-only views of a plan (plan.cu).
 const DevObs *plan_devobs(psf_plan_t p);
 uint32_t plan_flags(psf_plan_t p);
+int plan_device(psf_plan_t p);   // device the plan's arrays live on (-1 for NULL)
 
 // ---- gridded image-plane approximation (k_grid.cu) -------------------------
 // One position of the gridded transform: c = (coefficient of a', coefficient of b',

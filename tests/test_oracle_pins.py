@@ -334,3 +334,43 @@ def test_p3_unequal_contiguous_channels():
         ref = np.exp(-2j * np.pi * (nu_mid - nu_r) * X / C) * np.sinc(X * dnu / C)
         D = oracle.decorr(obs, oracle.EXACT, l0, 0.0)[0]
         assert abs(D - ref) < 1e-12
+
+
+# ----------------------------------------------------------------- Algorithm 1, printed theta
+def _dsinc(y):
+    return 0.0 if y == 0 else (math.cos(math.pi * y) - np.sinc(y)) / y
+
+
+@pytest.mark.parametrize("uv", [(0.0, 3000.0), (0.0, -2500.0), (4000.0, 0.0), (-1800.0, 0.0)])
+def test_literal_theta_closed_forms(uv):
+    """Algorithm 1's printed theta = arctan(u/v) (Sect. 3.2), pinned on baselines along the
+    axes, where the arctangent is fixed: u = 0 gives theta = 0 and (du/dt, dv/dt) =
+    omega_E |uv| (-sin theta, cos theta) = omega_E (0, |v|), so dPsi/(2 pi) =
+    omega_E Dt |v| m0; v = 0 gives theta = +-pi/2 and dPsi/(2 pi) = -+omega_E Dt |u| l0.
+    D = sinc_pi(dPsi / 2 pi) sinc_pi((Dnu/nu) |uv| rho) and its l0, m0 derivatives in
+    closed form.  The default reading theta = atan2(v, u) pairs the other way (u = 0:
+    dPsi/(2 pi) = -omega_E Dt v l0), so a swapped sine and cosine in either branch fails."""
+    u, v = uv
+    nu, width, ntime = 1.4e9, 2e6, 100
+    dt = float(ntime)                                 # one bin of 100 samples of 1 s
+    l0, m0 = 0.031, -0.017
+    rho = math.hypot(l0, m0)
+    obs = _static_obs([(u, v)], nu, ntime=ntime, width=width)
+    uvlen = math.hypot(u, v)
+    w = obsgen.OMEGA_E * dt
+    if u == 0.0:
+        A, Al, Am = w * abs(v) * m0, 0.0, w * abs(v)
+        A_def = -w * v * l0
+    else:
+        A, Al, Am = -w * u * l0, -w * u, 0.0
+        A_def = w * u * m0
+    B = width / nu * uvlen * rho
+    Bl, Bm = width / nu * uvlen * l0 / rho, width / nu * uvlen * m0 / rho
+    D, g = oracle.decorr(obs, oracle.IMG, l0, m0, flags=oracle.LITERAL_THETA, grad=True)
+    assert abs(D[0] - np.sinc(A) * np.sinc(B)) < 1e-13
+    assert abs(D[0].imag) == 0.0
+    assert abs(g[0, 0] - (_dsinc(A) * Al * np.sinc(B) + np.sinc(A) * _dsinc(B) * Bl)) < 1e-11
+    assert abs(g[0, 2] - (_dsinc(A) * Am * np.sinc(B) + np.sinc(A) * _dsinc(B) * Bm)) < 1e-11
+    D_def = oracle.decorr(obs, oracle.IMG, l0, m0)
+    assert abs(D_def[0] - np.sinc(A_def) * np.sinc(B)) < 1e-13
+    assert abs(D_def[0] - D[0]) > 1e-3   # the two readings differ on these baselines
