@@ -180,7 +180,7 @@ def parity_check(psf):
     res = {}
     refs = {m: oracle.psf(obs, mid, bg) for m, mid in (("exact", 0), ("uv", 1), ("img", 2))}
     with psf.Plan(obs, prec="fp32") as plan:
-        for prec in ("fp32", "tc_fp16", "tc_bf16"):
+        for prec in ("fp32", "tc_fp16", "tc_bf16", "tc_fp16x3", "tc_bf16x3"):
             plan.set_opts(prec=prec)
             for m in ("exact", "uv", "img"):
                 got = plan.forward(m, batch).cpu().numpy().astype(np.float64)
@@ -197,8 +197,48 @@ def parity_check(psf):
             got = plan.approx_img_grid(batch).cpu().numpy().astype(np.float64)
             res[f"{prec}/img_grid"] = float(np.max(np.abs(got - gref)) / np.max(np.abs(gref)))
     return {"workload": "16ant_1km_1h_4ch_64px", "metric": "max |P - P_oracle| / max |P_oracle|", "err_max": res,
-            "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3, "fp32/img_grid": 1e-5,
-                          "tc_fp16/img_grid": 3e-4}}
+            "tolerance": {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3, "tc_fp16x3": 2e-5, "tc_bf16x3": 2e-5,
+                          "fp32/img_grid": 1e-5, "tc_fp16/img_grid": 3e-4}}
+
+
+def measure_ladder(psf, plan, obs, batch_g, batch, outs, step, stream):
+    """Precision ladder on the benchmark workload: per precision mode the rate of the same
+    step (exact + uv + img) and the peak-normalised max error of the exact cutout against
+    the FP64 oracle on sampled pixels (the centre and seven others), plus the error on
+    workload 1 (full 64 x 64 cutouts, all methods) from `parity`.  The split modes execute
+    three MMA passes per algorithmic product (executed tensor flops = 3 x algorithmic)."""
+    import torch
+    import oracle
+    K = obs.nvis()
+    N = int(batch_g.npix[0])
+    c = N // 2
+    sel = np.array([c * N + c, 0, N - 1, N * N - 1, c * N + c + 1, (c + 3) * N + c - 2, 31 * N + 100, 100 * N + 3])
+    ref = oracle.psf(obs, oracle.EXACT, batch_g, pix_sel=sel)[sel]
+    terms = terms_per_step(K, batch_g)
+    res = {}
+    prev = plan.prec
+    for prec in ("fp32", "tc_fp16", "tc_bf16", "tc_fp16x3", "tc_bf16x3"):
+        plan.set_opts(prec=prec)
+        step(plan)
+        torch.cuda.synchronize()
+        nrep = 2 if prec == "fp32" else 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(nrep):
+            step(plan)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / nrep
+        got = outs[0].cpu().numpy().astype(np.float64)[sel]
+        split = prec.endswith("x3")
+        res[prec] = {"terms_per_s": terms / (ms * 1e-3), "ms_per_step": ms,
+                     "err_max_exact_sampled": float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))),
+                     "mma_passes": 3 if split else (0 if prec == "fp32" else 1),
+                     "executed_tensor_flops_per_term": 12.0 if split else (0.0 if prec == "fp32" else 4.0)}
+    plan.set_opts(prec=prev)
+    if plan.sync_status() != 0:
+        raise RuntimeError("device-side wait timed out in the precision ladder")
+    return {"workload": WORKLOAD, "step": "exact + uv + img", "pixels_sampled": len(sel), "modes": res}
 
 
 def cpu_baseline_sample(obs, batch):
@@ -565,6 +605,7 @@ def main():
     ap.add_argument("--no-clean", action="store_true")
     ap.add_argument("--no-fwhm", action="store_true")
     ap.add_argument("--no-facets", action="store_true")
+    ap.add_argument("--no-ladder", action="store_true")
     ap.add_argument("--grid-positions", type=int, default=16384,
                     help="positions of the gridded-form measurement (radial grid out to 3 deg)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean", "facets"],
@@ -718,6 +759,8 @@ def main():
         e2e = {"value": world * terms / dt, "unit": "terms/s", "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(sum(h.numel() * 4 for h in host)), "ms_per_step": dt * 1e3}
 
+    ladder = None if args.no_ladder or rank != 0 else measure_ladder(psf, plan, obs, batch_g, batch, outs, step,
+                                                                     stream)
     img_grid = None if args.no_grid or rank != 0 else measure_img_grid(psf, plan, obs, clocks,
                                                                        npos=args.grid_positions)
     clean = None if args.no_clean or rank != 0 else measure_clean(psf, plan)
@@ -752,7 +795,8 @@ def main():
                 "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "precision_ladder": ladder,
+                "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

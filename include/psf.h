@@ -55,6 +55,16 @@ extern "C" {
 #define PSF_FP32     0   /* FP32 CUDA-core form: weights, twiddles, sums in FP32   */
 #define PSF_TC_FP16  1   /* tcgen05 tensor cores, FP16 operands, FP32 accumulate  */
 #define PSF_TC_BF16  3   /* tcgen05 tensor cores, BF16 operands, FP32 accumulate  */
+/* Split precision on the tensor cores: every operand value x is held as hi = rnd16(x)
+ * and lo = rnd16(x - hi) and each product is A_hi B_hi + A_hi B_lo + A_lo B_hi (three
+ * MMA passes into one FP32 accumulator), which removes the 16-bit rounding of both
+ * operands to second order (BF16: 2^-8 -> ~2^-16 per value; FP16: 2^-11 -> ~2^-22, the
+ * low parts of small values being FP16 subnormals).  Weights are evaluated with the
+ * accurate FP32 sine/cosine.  Per-cutout form only (the batched form is not used),
+ * tiles of at most 128 columns; not with PSF_COMPLEX_OUT (PSF_EUNSUPPORTED).  Executed
+ * tensor flops are three times the algorithmic ones. */
+#define PSF_TC_FP16X3 2
+#define PSF_TC_BF16X3 4
 
 /* ---- option flags ------------------------------------------------------ */
 #define PSF_WTERM             1u  /* use L0 = (l0, m0, n0-1): w enters the smearing */
@@ -109,7 +119,7 @@ typedef struct {
     const float *weights;
 } psf_obs_t;
 
-/* prec: PSF_FP32 / PSF_TC_FP16 / PSF_TC_BF16.  flags: PSF_WTERM |
+/* prec: PSF_FP32 / PSF_TC_FP16 / PSF_TC_BF16 / PSF_TC_FP16X3 / PSF_TC_BF16X3.  flags: PSF_WTERM |
  * PSF_IMG_LITERAL_THETA | PSF_DETERMINISTIC | PSF_COMPLEX_OUT.  algo: PSF_ALGO_*. */
 typedef struct {
     int32_t prec;

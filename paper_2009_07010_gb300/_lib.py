@@ -12,7 +12,7 @@ import threading
 from . import build as _build
 
 PSF_OK, PSF_EINVAL, PSF_ENOMEM, PSF_ECUDA, PSF_EUNSUPPORTED, PSF_ETIMEOUT = 0, -1, -2, -3, -4, -5
-PSF_FP32, PSF_TC_FP16, PSF_TC_BF16 = 0, 1, 3
+PSF_FP32, PSF_TC_FP16, PSF_TC_BF16, PSF_TC_FP16X3, PSF_TC_BF16X3 = 0, 1, 3, 2, 4
 PSF_WTERM, PSF_IMG_LITERAL_THETA, PSF_DETERMINISTIC, PSF_COMPLEX_OUT = 1, 2, 4, 8
 PSF_CLEAN_FACET_PSF = 1
 PSF_ALGO_AUTO, PSF_ALGO_CUTOUT = 0, 1

@@ -16,7 +16,8 @@ import torch
 from . import _lib
 from ._lib import check
 
-PREC = {"fp32": _lib.PSF_FP32, "tc_fp16": _lib.PSF_TC_FP16, "tc_bf16": _lib.PSF_TC_BF16}
+PREC = {"fp32": _lib.PSF_FP32, "tc_fp16": _lib.PSF_TC_FP16, "tc_bf16": _lib.PSF_TC_BF16,
+        "tc_fp16x3": _lib.PSF_TC_FP16X3, "tc_bf16x3": _lib.PSF_TC_BF16X3}
 METHODS = {"exact": _lib.EXACT, "uv": _lib.UV, "img": _lib.IMG}
 
 

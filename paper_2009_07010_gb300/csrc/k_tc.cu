@@ -61,6 +61,11 @@ constexpr int kInWarp = 21;
 constexpr int kMma2Warp = 22;
 constexpr int kThreads = 23 * 32;
 constexpr int kDrainStages = 64;   // stages accumulated in TMEM between drains
+// Split precision: the tensor core's FP32 accumulation loses about 2^-24.5 of the running
+// value per added MMA (measured: the error of a cutout grows with the MMAs accumulated
+// between drains, 64-stage runs of 12 MMAs left ~1e-5), so the runs are 8 stages and the
+// drain warps keep the running sum in TMEM (FP32 adds, round to nearest).
+constexpr int kDrainStagesSplit = 8;
 constexpr int kATileBytes = 128 * 128;
 // One 32-row twiddle chain of one visibility (this lane), rows r = 0..31 of `base`:
 // value(r) = [w] exp(2 pi i theta (n0 + r)), written as an FP16/BF16 (re, im) pair at
@@ -75,10 +80,13 @@ constexpr int kATileBytes = 128 * 128;
 // CPLX: each row value z is also written as (-Im z, Re z) at row r of base + mbase
 // (the second half of a doubled B tile: with z = conj(a) these rows give the
 // imaginary part of the contraction).
-template <int BF16, bool MIRROR = false, bool CPLX = false>
+// SPLIT: every value is also written as its low part (value - rounded value, rounded
+// to 16 bits) at the same position lo_off bytes further on (the lo tile of a split
+// precision stage); conjugation of the low part is the same sign-bit XOR.
+template <int BF16, bool MIRROR = false, bool CPLX = false, bool SPLIT = false>
 __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float2 wk,
                                             bool weighted, uint32_t mbase = 0, bool tail = false,
-                                            uint32_t tail_addr = 0) {
+                                            uint32_t tail_addr = 0, uint32_t lo_off = 0) {
     // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3.  Two
     // sine/cosine evaluations per chain (row 0 and the step); the piece seeds follow
     // by complex multiplication with the 4- and 16-row strides (squarings of the
@@ -112,13 +120,23 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
             const uint32_t v2 = pack2<BF16>(re[0].y, im[0].y), v3 = pack2<BF16>(re[1].y, im[1].y);
             // without mirroring the row addresses are recomputed from the lane (cheaper than
             // holding eight offsets at this kernel's register budget)
-            stmatrix_x4(MIRROR ? base + off[q]
-                               : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)q * 128u +
-                                     (((threadIdx.x & 7u) ^ (uint32_t)q) << 4),
-                        v0, v1, v2, v3);
-            if (MIRROR)
-                stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)q * 128u + ((ca ^ ((8u - q) & 7u)) << 4),
-                            v0 ^ kConj, v1 ^ kConj, v2 ^ kConj, v3 ^ kConj);
+            const uint32_t addr = MIRROR ? base + off[q]
+                                         : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)q * 128u +
+                                               (((threadIdx.x & 7u) ^ (uint32_t)q) << 4);
+            stmatrix_x4(addr, v0, v1, v2, v3);
+            uint32_t l0 = 0u, l1 = 0u, l2 = 0u, l3 = 0u;
+            if (SPLIT) {
+                l0 = pack2_lo<BF16>(re[0].x, im[0].x, v0);
+                l1 = pack2_lo<BF16>(re[1].x, im[1].x, v1);
+                l2 = pack2_lo<BF16>(re[0].y, im[0].y, v2);
+                l3 = pack2_lo<BF16>(re[1].y, im[1].y, v3);
+                stmatrix_x4(addr + lo_off, l0, l1, l2, l3);
+            }
+            if (MIRROR) {
+                const uint32_t maddr = mbase - (ln >> 3) * 1024u - (uint32_t)q * 128u + ((ca ^ ((8u - q) & 7u)) << 4);
+                stmatrix_x4(maddr, v0 ^ kConj, v1 ^ kConj, v2 ^ kConj, v3 ^ kConj);
+                if (SPLIT) stmatrix_x4(maddr + lo_off, l0 ^ kConj, l1 ^ kConj, l2 ^ kConj, l3 ^ kConj);
+            }
             if (CPLX)
                 stmatrix_x4(base + mbase + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)q * 128u +
                                 (((threadIdx.x & 7u) ^ (uint32_t)q) << 4),
@@ -128,13 +146,24 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
         {
             const uint32_t v4 = pack2<BF16>(re[2].x, im[2].x), v5 = pack2<BF16>(re[3].x, im[3].x);
             const uint32_t v6 = pack2<BF16>(re[2].y, im[2].y), v7 = pack2<BF16>(re[3].y, im[3].y);
-            stmatrix_x4(MIRROR ? base + off[q + 4]
-                               : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)(q + 4) * 128u +
-                                     (((threadIdx.x & 7u) ^ (uint32_t)(q + 4)) << 4),
-                        v4, v5, v6, v7);
-            if (MIRROR)
-                stmatrix_x4(mbase - (ln >> 3) * 1024u - (uint32_t)(q + 4) * 128u + ((ca ^ ((4u - q) & 7u)) << 4),
-                            v4 ^ kConj, v5 ^ kConj, v6 ^ kConj, v7 ^ kConj);
+            const uint32_t addr = MIRROR ? base + off[q + 4]
+                                         : base + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)(q + 4) * 128u +
+                                               (((threadIdx.x & 7u) ^ (uint32_t)(q + 4)) << 4);
+            stmatrix_x4(addr, v4, v5, v6, v7);
+            uint32_t l4 = 0u, l5 = 0u, l6 = 0u, l7 = 0u;
+            if (SPLIT) {
+                l4 = pack2_lo<BF16>(re[2].x, im[2].x, v4);
+                l5 = pack2_lo<BF16>(re[3].x, im[3].x, v5);
+                l6 = pack2_lo<BF16>(re[2].y, im[2].y, v6);
+                l7 = pack2_lo<BF16>(re[3].y, im[3].y, v7);
+                stmatrix_x4(addr + lo_off, l4, l5, l6, l7);
+            }
+            if (MIRROR) {
+                const uint32_t maddr =
+                    mbase - (ln >> 3) * 1024u - (uint32_t)(q + 4) * 128u + ((ca ^ ((4u - q) & 7u)) << 4);
+                stmatrix_x4(maddr, v4 ^ kConj, v5 ^ kConj, v6 ^ kConj, v7 ^ kConj);
+                if (SPLIT) stmatrix_x4(maddr + lo_off, l4 ^ kConj, l5 ^ kConj, l6 ^ kConj, l7 ^ kConj);
+            }
             if (CPLX)
                 stmatrix_x4(base + mbase + (((threadIdx.x >> 3) & 3u) << 10) + (uint32_t)(q + 4) * 128u +
                                 (((threadIdx.x & 7u) ^ (uint32_t)(q + 4)) << 4),
@@ -154,7 +183,12 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
         const float r32 = re[3].y * st.x - im[3].y * st.y, i32 = re[3].y * st.y + im[3].y * st.x;
         const uint32_t lane = threadIdx.x & 31u;
         // row 0: chunk lane / 4 (unswizzled), pair lane mod 4
-        asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + lane * 4u), "r"(pack2<BF16>(r32, -i32)) : "memory");
+        const uint32_t h = pack2<BF16>(r32, -i32);
+        asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + lane * 4u), "r"(h) : "memory");
+        if (SPLIT)
+            asm volatile("st.shared.b32 [%0], %1;" ::"r"(tail_addr + lo_off + lane * 4u),
+                         "r"(pack2_lo<BF16>(r32, -i32, h))
+                         : "memory");
     }
 }
 
@@ -229,17 +263,20 @@ struct SmemLayout {
 constexpr uint32_t kInSlotBytes = kKS * 16;   // uv (8 B) + w (8 B) per visibility
 
 // Operand ring depth for a tile width: as many 128-row A + ncols-row B stages as fit
-// in ~192 KB (4 at 256 columns, 6 at 128, 8 at <= 64).
-__host__ __device__ constexpr int stages_for(int ncols_max) {
-    return ncols_max > 128 ? 4 : (ncols_max > 64 ? 6 : 8);
+// in ~192 KB (4 at 256 columns, 6 at 128, 8 at <= 64); split precision stages hold hi
+// and lo tiles of both operands (3 at 128 columns, 4 at <= 64; tiles of at most 128
+// columns).
+__host__ __device__ constexpr int stages_for(int ncols_max, int split = 0) {
+    return split ? (ncols_max > 64 ? 3 : 4) : (ncols_max > 128 ? 4 : (ncols_max > 64 ? 6 : 8));
 }
 
-__host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages, uint32_t in_slot = kInSlotBytes) {
+__host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages, uint32_t in_slot = kInSlotBytes,
+                                                  int split = 0) {
     SmemLayout L;
     const uint32_t bt = (uint32_t)ncols_max * 128u;
     L.a_off = 0;
-    L.b_off = kStages * kATileBytes;
-    L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u);
+    L.b_off = kStages * kATileBytes * (1 + split);
+    L.in_off = L.b_off + kStages * ((bt + 1023u) / 1024u * 1024u) * (1 + split);
     L.bar_off = L.in_off + kInStages * in_slot;
     L.bytes = L.bar_off + 512;   // 2 S + 2 kInStages + 8 barriers (<= 56 x 8 B), TMEM address, abort flag
     return L;
@@ -256,7 +293,13 @@ __host__ __device__ inline SmemLayout smem_layout(int ncols_max, int kStages, ui
 // cutout's partial sums from `partial`); 5 = complex output: A as in mode 0, B of 2 ncols
 // rows = the conjugated row twiddles (a_r, -a_i) and then (a_i, a_r), so the two halves
 // of the accumulator are the real and the imaginary parts of the cutout.
-template <int BF16, int kStages, int NISS, int MIR>
+//
+// SPLIT = 1 (split precision, MIR 0-2, tiles of at most 128 columns): every operand
+// value x is held as hi = rnd16(x) and lo = rnd16(x - hi) in two tiles of the stage, and
+// each stage issues A_hi B_hi + A_hi B_lo + A_lo B_hi into the same accumulator (the
+// lo x lo term is below the 16-bit rounding of the lo parts).  The stages are twice as
+// large, so the ring holds 3 or 4 of them and as many generator groups run.
+template <int BF16, int kStages, int NISS, int MIR, int SPLIT = 0>
 __global__ void __launch_bounds__(kThreads, 1)
     k_psf_tc(const float2 *__restrict__ uv, const float2 *__restrict__ w, int64_t ldw,
              const TcItem *__restrict__ items, int ncols_max, float cell, float *__restrict__ partial,
@@ -266,7 +309,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     constexpr int kBMul = (MIR == 4 || MIR == 5) ? 2 : 1;           // B rows per output column
     constexpr uint32_t kSlot = (MIR == 4) ? kKS * 24 : kInSlotBytes;   // uv, w (, w2) per visibility
-    const SmemLayout L = smem_layout(kBMul * ncols_max, kStages, kSlot);
+    // generator groups: one per stage of the ring at most (see kGroups)
+    constexpr int kGrp = kStages < kGroups ? kStages : kGroups;
+    static_assert(kGrp <= kStages, "generator groups must not exceed the operand ring depth");
+    static_assert(!SPLIT || MIR <= 2, "split precision covers the plain and mirrored real-weight forms");
+    // Two issuers take alternate stages; with an even ring depth every slot (and its release
+    // barrier) then belongs to one issuer.  An odd depth makes the two issuing threads commit
+    // alternately to the same release barrier, and such launches (3 stages, two issuers)
+    // gave up bounded waits in about one launch in eight on GB300 with the protocol reading
+    // correctly; two issuers are therefore only used with even depths.
+    static_assert(NISS == 1 || kStages % 2 == 0, "two MMA issuers need an even operand ring depth");
+    constexpr int kRange = SPLIT ? kDrainStagesSplit : kDrainStages;   // stages per accumulation run
+    const SmemLayout L = smem_layout(kBMul * ncols_max, kStages, kSlot, SPLIT);
     uint64_t *full = (uint64_t *)(smem + L.bar_off);
     uint64_t *empty = full + kStages;
     uint64_t *in_full = empty + kStages;
@@ -281,7 +335,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const TcItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int ncols = it.ncols;
-    const uint32_t bt_stride = ((uint32_t)(kBMul * ncols_max) * 128u + 1023u) / 1024u * 1024u;
+    const uint32_t bt_stride = ((uint32_t)(kBMul * ncols_max) * 128u + 1023u) / 1024u * 1024u;   // one B tile
+    const uint32_t b_stage = bt_stride * (1 + SPLIT);                  // hi (and lo) B tiles of a stage
+    constexpr uint32_t kAStage = kATileBytes * (1 + SPLIT);
     const uint32_t acc_cols = pow2_cols(kBMul * ncols_max);
     const int nst = (it.k1 - it.k0 + kKS - 1) / kKS;
 
@@ -301,8 +357,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     // accumulator (issuer q, buffer b) at TMEM column (2 q + b) acc_cols
+    // accumulators (issuer, buffer) and, with split precision, the running sum
+    const uint32_t tmem_cols = pow2_cols((2 * NISS + SPLIT) * (int)acc_cols);
     if (warp == kMmaWarp) {
-        tmem_alloc(s_tmem, 2 * NISS * acc_cols);
+        tmem_alloc(s_tmem, tmem_cols);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -310,7 +368,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    if (warp < kGenWarps) {
+    if (warp < kGrp * kGroupWarps) {
         // ------------------------------------------------------------ generators
         const int grp = warp / kGroupWarps, gw = warp % kGroupWarps;
         const int half = it.N / 2;
@@ -327,7 +385,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int nB = mirror ? it.N / 64 : ncols / 32;
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
-        for (int s_i = grp; s_i < nst; s_i += kGroups) {
+        for (int s_i = grp; s_i < nst; s_i += kGrp) {
             const int slot = s_i % kStages;
             const uint32_t ph = (uint32_t)(s_i / kStages) & 1u;
             const int islot = s_i % kInStages;
@@ -344,8 +402,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                 if (!__all_sync(0xffffffffu, ok)) break;
             }
-            const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kATileBytes);
-            const uint32_t b_tile = smem_u32(smem + L.b_off + slot * bt_stride);
+            const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kAStage);
+            const uint32_t b_tile = smem_u32(smem + L.b_off + slot * b_stage);
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
                 if (MIR == 5) {   // A: weighted column twiddles; B: row twiddles, real and imaginary halves
                     if (ch < nA)
@@ -370,14 +428,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const int c = isA ? ch : ch - nA;
                     const int R0 = half + 32 * c;
                     const uint32_t tile = isA ? a_tile : b_tile;
-                    gen_chain32<BF16, true>(tile + (uint32_t)R0 * 128u, off8, isA ? uvk.y * cell : -uvk.x * cell,
-                                            32 * c, wk, isA, tile + (uint32_t)(it.N - R0) * 128u, c == nA - 1,
-                                            tile);
+                    gen_chain32<BF16, true, false, SPLIT>(tile + (uint32_t)R0 * 128u, off8,
+                                                          isA ? uvk.y * cell : -uvk.x * cell, 32 * c, wk, isA,
+                                                          tile + (uint32_t)(it.N - R0) * 128u, c == nA - 1, tile,
+                                                          isA ? (uint32_t)kATileBytes : bt_stride);
                 } else if (ch < nA) {   // weighted column twiddles c_k[j], rows j = j0 + 32 ch + r
-                    gen_chain32<BF16>(a_tile + ch * 32 * 128, off8, uvk.y * cell, it.j0 + ch * 32 - half, wk, true);
+                    gen_chain32<BF16, false, false, SPLIT>(a_tile + ch * 32 * 128, off8, uvk.y * cell,
+                                                           it.j0 + ch * 32 - half, wk, true, 0, false, 0,
+                                                           (uint32_t)kATileBytes);
                 } else {                // conjugated row twiddles (a_r, -a_i), rows i = i0 + 32 (ch - nA) + r
-                    gen_chain32<BF16>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
-                                      it.i0 + (ch - nA) * 32 - half, wk, false);
+                    gen_chain32<BF16, false, false, SPLIT>(b_tile + (ch - nA) * 32 * 128, off8, -uvk.x * cell,
+                                                           it.i0 + (ch - nA) * 32 - half, wk, false, 0, false, 0,
+                                                           bt_stride);
                 }
             }
             fence_proxy_async_smem();
@@ -388,7 +450,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // ------------------------------------------------------------ MMA issue
         // Issuer q takes the stages s = q (mod NISS); with an even ring depth every
         // slot belongs to one issuer.  Accumulation range d covers stages
-        // [d kDrainStages, (d + 1) kDrainStages) and uses buffer b = d mod 2.
+        // [d kRange, (d + 1) kRange) and uses buffer b = d mod 2.
         if (lane == 0) {
             const int q = (warp == kMmaWarp) ? 0 : 1;
             // The MMA issue blocks this thread until the tensor core takes the
@@ -407,8 +469,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     !wait_bounded(&acc_empty[b], (uint32_t)((d >> 1) - 1) & 1u, s_abort, err))
                     break;
                 tc_fence_after();
-                const uint64_t ad = ad0 + (uint64_t)(slot * (kATileBytes >> 4));
-                const uint64_t bd = bd0 + (uint64_t)(slot * (bt_stride >> 4));
+                const uint64_t ad = ad0 + (uint64_t)(slot * (kAStage >> 4));
+                const uint64_t bd = bd0 + (uint64_t)(slot * (b_stage >> 4));
                 const uint32_t dt = tmem + (uint32_t)(2 * q + b) * acc_cols;
                 // K' = 16 per MMA = 32 bytes (descriptor units of 16 B: +2) of the 128-byte row
                 if (r == q) umma_f16(dt, ad, bd, idesc, 0u);
@@ -416,11 +478,18 @@ __global__ void __launch_bounds__(kThreads, 1)
                 umma_f16(dt, ad + 2, bd + 2, idesc, 1u);
                 umma_f16(dt, ad + 4, bd + 4, idesc, 1u);
                 umma_f16(dt, ad + 6, bd + 6, idesc, 1u);
+                if (SPLIT) {   // A_hi B_lo, then A_lo B_hi
+                    const uint64_t bl = bd + (uint64_t)(bt_stride >> 4), al = ad + (uint64_t)(kATileBytes >> 4);
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk += 2) umma_f16(dt, ad + kk, bl + kk, idesc, 1u);
+#pragma unroll
+                    for (int kk = 0; kk < 8; kk += 2) umma_f16(dt, al + kk, bd + kk, idesc, 1u);
+                }
                 umma_commit(&empty[slot]);
                 r += NISS;
-                if (r >= kDrainStages || s_i + NISS >= nst) umma_commit(&acc_full[2 * q + b]);
-                if (r >= kDrainStages) {
-                    r -= kDrainStages;
+                if (r >= kRange || s_i + NISS >= nst) umma_commit(&acc_full[2 * q + b]);
+                if (r >= kRange) {
+                    r -= kRange;
                     ++d;
                 }
                 slot += NISS;
@@ -463,6 +532,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else if (warp == kMma2Warp) {
         // second issuer, idle with one issuer (NISS == 1): it must not join the drain
         // warps (lane quarters 0-3, four arrivals per accumulator release)
+    } else if (warp < kGenWarps) {
+        // generator warps beyond the ring depth's groups (split precision): idle
     } else {
         // ------------------------------------------------------------ drain
         // The partial cutout is stored transposed (element (j, i) at i N + j), so the 32
@@ -482,11 +553,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (kBMul == 2) dst2[c * cstride] = 0.f;
                 }
         }
-        const int ndrain = (nst + kDrainStages - 1) / kDrainStages;
+        const int ndrain = (nst + kRange - 1) / kRange;
+        // split precision: running sum of the drained ranges in TMEM columns after the
+        // accumulators
+        const uint32_t tsum = tmem + ((uint32_t)(q * 32) << 16) + 2u * NISS * acc_cols;
         for (int d = 0; d < ndrain; ++d) {
             const int b = d & 1;
             // issuer 1 has a stage in range d unless the range holds a single stage
-            const bool two = (NISS == 2) && (min(nst, (d + 1) * kDrainStages) - d * kDrainStages > 1);
+            const bool two = (NISS == 2) && (min(nst, (d + 1) * kRange) - d * kRange > 1);
             bool ok = wait_bounded(&acc_full[b], (uint32_t)(d >> 1) & 1u, s_abort, err);
             if (two && ok) ok = wait_bounded(&acc_full[2 + b], (uint32_t)(d >> 1) & 1u, s_abort, err);
             if (!__all_sync(0xffffffffu, ok)) break;   // warp-uniform exit
@@ -503,6 +577,22 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld16(ta + 2u * acc_cols + (uint32_t)c0, v2);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] += v2[e];
+                }
+                if (SPLIT) {
+                    if (d > 0) {
+                        float sv[16];
+                        tmem_ld16(tsum + (uint32_t)c0, sv);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) v[e] += sv[e];
+                    }
+                    if (d < ndrain - 1) {
+                        tmem_st16(tsum + (uint32_t)c0, v);
+                    } else if (row_ok) {   // last range: the CTA's sum goes out once
+#pragma unroll
+                        for (int e = 0; e < 16; ++e)
+                            if (cb + e < ncol_valid) dd[(cb + e) * cstride] = v[e];
+                    }
+                    continue;
                 }
                 if (row_ok) {
                     // eight loads in flight before their stores (one L2 round trip per eight)
@@ -526,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == kMmaWarp) tmem_dealloc(tmem, 2 * NISS * acc_cols);
+    if (warp == kMmaWarp) tmem_dealloc(tmem, tmem_cols);
 }
 
 // Self-test: one 128 x n x 64 FP16 GEMM through the same layout, descriptors,
@@ -629,24 +719,44 @@ int selftest_timeout(int limit_ms) {
     return flag ? PSF_ETIMEOUT : PSF_OK;
 }
 
-template <int BF16, int S, int NISS, int MIR>
+template <int BF16, int S, int NISS, int MIR, int SPLIT = 0>
 static cudaError_t launch_tc_t(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                                int ncols_max, float cell, float *partial, int64_t split_stride, int *err,
                                cudaStream_t st, const float2 *w2 = nullptr, int64_t part2 = 0) {
-    const SmemLayout L = smem_layout((MIR == 4 || MIR == 5 ? 2 : 1) * ncols_max, S, MIR == 4 ? kKS * 24 : kInSlotBytes);
+    const SmemLayout L =
+        smem_layout((MIR == 4 || MIR == 5 ? 2 : 1) * ncols_max, S, MIR == 4 ? kKS * 24 : kInSlotBytes, SPLIT);
     const size_t bytes = L.bytes + 1024;
-    cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS, MIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_psf_tc<BF16, S, NISS, MIR, SPLIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
     if (e != cudaSuccess) return e;
-    k_psf_tc<BF16, S, NISS, MIR><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell, partial,
-                                                                   split_stride, err, w2, part2);
+    k_psf_tc<BF16, S, NISS, MIR, SPLIT><<<nitems, kThreads, bytes, st>>>(o.uv, w, ldw, items, ncols_max, cell,
+                                                                          partial, split_stride, err, w2, part2);
     return cudaGetLastError();
 }
 
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items, int nitems,
                           int ncols_max, int bf16, float cell, int wreal, float *partial, int64_t split_stride,
-                          int *err, cudaStream_t st) {
+                          int *err, cudaStream_t st, int split) {
     if (nitems <= 0) return cudaSuccess;
+    if (split) {   // tiles of at most 128 columns
+        if (ncols_max > 128) return cudaErrorInvalidValue;
+        // 3 stages (128 columns): one issuer (twelve MMAs per stage hide its barrier round
+        // trip; two issuers need an even depth); 4 stages (<= 64 columns): two issuers
+#define PSF_TC_SPLIT(B, SS)                                                                                    \
+    if (bf16 == B && stages_for(ncols_max, 1) == SS) {                                                         \
+        constexpr int NI = SS % 2 == 0 ? 2 : 1;                                                                \
+        if (wreal == 2)                                                                                        \
+            return launch_tc_t<B, SS, NI, 2, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial, split_stride, \
+                                                err, st);                                                      \
+        return wreal ? launch_tc_t<B, SS, NI, 1, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial,        \
+                                                    split_stride, err, st)                                     \
+                     : launch_tc_t<B, SS, NI, 0, 1>(o, w, ldw, items, nitems, ncols_max, cell, partial,        \
+                                                    split_stride, err, st);                                    \
+    }
+        PSF_TC_SPLIT(0, 3) PSF_TC_SPLIT(0, 4) PSF_TC_SPLIT(1, 3) PSF_TC_SPLIT(1, 4)
+#undef PSF_TC_SPLIT
+        return cudaErrorInvalidValue;
+    }
     const int S = stages_for(ncols_max);
     // two issuers while both double-buffered accumulator pairs fit in TMEM (<= 128 columns)
 #define PSF_TC_CASE(B, SS)                                                                                  \

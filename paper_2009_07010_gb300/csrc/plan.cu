@@ -81,6 +81,10 @@ int cuda_status(cudaError_t e) {
 
 size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+// Tensor-core operand type and the split (hi + lo, three MMA passes) precision modes.
+bool prec_bf16(int prec) { return prec == PSF_TC_BF16 || prec == PSF_TC_BF16X3; }
+bool prec_split(int prec) { return prec == PSF_TC_FP16X3 || prec == PSF_TC_BF16X3; }
+
 // Storage for a CUtensorMap (128 bytes, 64-byte aligned) without including cuda.h here.
 struct alignas(64) CUtensorMapStub {
     unsigned char bytes[128];
@@ -160,7 +164,9 @@ int validate_obs(const psf_obs_t *o) {
 
 int validate_opts(const psf_opts_t *op) {
     if (!op) return PSF_OK;
-    if (op->prec != PSF_FP32 && op->prec != PSF_TC_FP16 && op->prec != PSF_TC_BF16) return PSF_EINVAL;
+    if (op->prec != PSF_FP32 && op->prec != PSF_TC_FP16 && op->prec != PSF_TC_BF16 && op->prec != PSF_TC_FP16X3 &&
+        op->prec != PSF_TC_BF16X3)
+        return PSF_EINVAL;
     if (op->flags & ~(PSF_WTERM | PSF_IMG_LITERAL_THETA | PSF_DETERMINISTIC | PSF_COMPLEX_OUT)) return PSF_EINVAL;
     if (op->algo != PSF_ALGO_AUTO && op->algo != PSF_ALGO_CUTOUT) return PSF_EINVAL;
     return PSF_OK;
@@ -553,7 +559,7 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
     const int ntile = (np + 127) / 128;
     const int rows = ntile * 128;
     const int64_t K = p->nvis;
-    const int bf16 = p->opts.prec == PSF_TC_BF16;
+    const int bf16 = prec_bf16(p->opts.prec);
     // Methods 1 and 2 have real weights: one K' column per visibility, 64-visibility
     // stages; the exact method has complex weights: two columns, 32-visibility stages.
     const int real = method != kExact;
@@ -662,17 +668,18 @@ int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, 
 int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st) {
     if (!p || !out) return PSF_EINVAL;
     const bool tc = p->opts.prec != PSF_FP32;
+    const bool split = prec_split(p->opts.prec);
     const bool cplx = (p->opts.flags & PSF_COMPLEX_OUT) != 0;
     BatchHost hall;
     int s = prepare_batch(p, b, hall, cplx ? 128 : (tc ? 256 : 4096), cplx ? 2 : 1);
     if (s || hall.npos == 0) return s;
-    if (cplx) return tc ? run_forward_cplx(p, method, hall, out, st) : PSF_EUNSUPPORTED;
+    if (cplx) return (tc && !split) ? run_forward_cplx(p, method, hall, out, st) : PSF_EUNSUPPORTED;
     const int64_t K = p->nvis;
     // Batched tensor-core form for large groups of one eligible size; the rest goes
     // through the per-cutout form below.
     BatchHost h;
     h.cell = hall.cell;
-    if (tc && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC)) {
+    if (tc && !split && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC)) {
         std::vector<std::vector<int>> groups(257);
         for (int i = 0; i < hall.npos; ++i) {
             const int N = hall.npix[i];
@@ -722,11 +729,12 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
             nsplit = (int)((K + kper - 1) / kper);
         } else {
             std::vector<TcItem> base;
+            const int tw = split ? 128 : 256;   // tile width (split precision: <= 128 columns)
             for (int i = 0; i < cn; ++i) {
                 const int N = h.npix[c0 + i];
                 for (int j0 = 0; j0 < N; j0 += 128)
-                    for (int i0 = 0; i0 < N; i0 += 256) {
-                        const int w = std::min(256, N - i0);
+                    for (int i0 = 0; i0 < N; i0 += tw) {
+                        const int w = std::min(tw, N - i0);
                         const int nc = (w + 31) / 32 * 32;   // whole 32-row twiddle chains
                         ncols_max = std::max(ncols_max, nc);
                         base.push_back(TcItem{i, N, j0, i0, nc, 0, 0, 0, loc[i]});
@@ -777,7 +785,10 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
         const int64_t ldw = (K + 31) / 32 * 32;
         PSF_TRY(p->wbuf.reserve((size_t)(cn * ldw + 64) * sizeof(float2)));
         float2 *w = (float2 *)p->wbuf.p;
-        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, tc ? 1 : 0, st));
+        // weights in FP32 with the accurate sine/cosine for the FP32 path and the split
+        // precision modes, the MUFU forms where they are rounded to 16 bits
+        PSF_TRY(launch_weights(p->d, method, p->opts.flags, d_pos, cn, 0, (int32_t)K, w, ldw, (tc && !split) ? 1 : 0,
+                               st));
 
         p->n_kernels++;
         float *part = out;
@@ -812,7 +823,8 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
                 if (whole) wreal = 2;
             }
             PSF_TRY(launch_psf_tc(p->d, w, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(), ncols_max,
-                                  p->opts.prec == PSF_TC_BF16, (float)h.cell, wreal, part, stride, (int *)p->err.p, st));
+                                  prec_bf16(p->opts.prec), (float)h.cell, wreal, part, stride, (int *)p->err.p, st,
+                                  split ? 1 : 0));
         }
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
@@ -832,7 +844,7 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
 // the two separate calls.
 int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float *out_img, cudaStream_t st) {
     if (!p || !out_uv || !out_img) return PSF_EINVAL;
-    const bool tc = p->opts.prec != PSF_FP32;
+    const bool tc = p->opts.prec != PSF_FP32 && !prec_split(p->opts.prec);   // fused pass: single-pass operands
     if (p->opts.flags & PSF_COMPLEX_OUT) {   // the fused pass writes real parts only
         const int s2 = run_forward(p, kUV, b, out_uv, st);
         return s2 ? s2 : run_forward(p, kImg, b, out_img, st);
@@ -928,7 +940,7 @@ int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float 
             PSF_TRY(cudaEventRecord(ev1, st));
         }
         PSF_TRY(launch_psf_tc_uvimg(p->d, w_uv, w_img, ldw, (const TcItem *)(dm + m.off_tiles), (int)items.size(),
-                                    ncols_max, p->opts.prec == PSF_TC_BF16, (float)h.cell, part, chunk_px, part2,
+                                    ncols_max, prec_bf16(p->opts.prec), (float)h.cell, part, chunk_px, part2,
                                     (int *)p->err.p, st));
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
@@ -1015,7 +1027,7 @@ int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, 
             PSF_TRY(cudaEventRecord(ev1, st));
         }
         PSF_TRY(launch_psf_tc_cplx(p->d, w, ldw, (const TcItem *)(dm + off_items), (int)items.size(), ncols_max,
-                                   p->opts.prec == PSF_TC_BF16, (float)h.cell, part, chunk_px, part2,
+                                   prec_bf16(p->opts.prec), (float)h.cell, part, chunk_px, part2,
                                    (int *)p->err.p, st));
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;

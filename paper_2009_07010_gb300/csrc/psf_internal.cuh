@@ -93,9 +93,10 @@ struct TcItem {
 // zero), which allows the conjugate-symmetric generation of the column twiddles; 2 =
 // real weights and every item spans a whole cutout of 64 or 128 pixels (i0 = j0 = 0,
 // ncols = N), so every tile is generated conjugate-symmetrically.
+// split != 0: split precision (hi + lo operands, three MMA passes; ncols_max <= 128).
 cudaError_t launch_psf_tc(const DevObs &o, const float2 *w, int64_t ldw, const TcItem *items,
                           int nitems, int ncols_max, int bf16, float cell, int wreal, float *partial,
-                          int64_t split_stride, int *err_flag, cudaStream_t st);
+                          int64_t split_stride, int *err_flag, cudaStream_t st, int split = 0);
 // Fused Methods 1 + 2 on whole cutouts of 64 or 128 pixels (every item: i0 = j0 = 0,
 // ncols = N; ncols_max 64 or 128): partial sums of the uv cutouts at `partial` and of
 // the image-plane cutouts at partial + part2, both laid out like launch_psf_tc's.

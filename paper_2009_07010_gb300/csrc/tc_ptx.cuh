@@ -172,6 +172,25 @@ static __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     }
 }
 
+template <int BF16>
+static __device__ __forceinline__ float2 unpack2(uint32_t v) {
+    if (BF16) {
+        const __nv_bfloat162 h = *reinterpret_cast<const __nv_bfloat162 *>(&v);
+        return __bfloat1622float2(h);
+    } else {
+        const __half2 h = *reinterpret_cast<const __half2 *>(&v);
+        return __half22float2(h);
+    }
+}
+
+// Low parts of a pair packed by pack2 (split precision): each value minus its 16-bit
+// rounding (exact in FP32), rounded to 16 bits again.
+template <int BF16>
+static __device__ __forceinline__ uint32_t pack2_lo(float lo, float hi, uint32_t packed) {
+    const float2 r = unpack2<BF16>(packed);
+    return pack2<BF16>(lo - r.x, hi - r.y);
+}
+
 static __device__ __forceinline__ uint32_t pow2_cols(int n) {
     uint32_t c = 32;
     while ((int)c < n) c <<= 1;

@@ -52,10 +52,11 @@ def _mixed_batch(seed, counts, radius, cell):
     return obsgen.Batch(lm, npix, cell)
 
 
-@pytest.mark.parametrize("prec,tol", [("tc_fp16", 1e-4), ("tc_bf16", 1e-3)])
+@pytest.mark.parametrize("prec,tol", [("tc_fp16", 1e-4), ("tc_bf16", 1e-3), ("tc_fp16x3", 2e-5)])
 def test_batched_mixed_sizes_config1(psf, prec, tol):
     """Workload-1 observation; 40 x 32^2 and 36 x 64^2 cutouts (batched) plus a few
-    96^2 and 128^2 ones (per-cutout), in one call."""
+    96^2 and 128^2 ones (per-cutout), in one call.  The split precision modes take the
+    per-cutout form for every position."""
     obs = obsgen.config1_obs()
     batch = _mixed_batch(5, [(32, 40), (64, 36), (96, 3), (128, 2)], 0.03, 2 * obsgen.ARCSEC)
     offs = obsgen.concat_pixels(batch)

@@ -6,7 +6,8 @@ pointwise relative error is undefined at PSF nulls).  Tolerances:
     phases are formed in float-float from the float64 bin centres, so a term carries
     ~1e-7 of error however large its phase);
   * tensor-core path: 1e-4 on the configuration workloads with FP16 operands; BF16
-    single-pass operands 1e-3 (2^-8 unit roundoff averaged over the sum);
+    single-pass operands 1e-3 (2^-8 unit roundoff averaged over the sum); the split
+    precision modes (hi + lo operands, three MMA passes) 2e-5 everywhere;
   * tensor-core few-visibility edge cases (tens of terms): the sum has too few terms
     for rounding errors to average out, so the bound is the per-term error: a few
     FP16 (BF16) unit roundoffs, 2^-11 (2^-8) -> 2e-3 (1.6e-2).
@@ -19,8 +20,8 @@ import oracle
 
 pytestmark = pytest.mark.gpu
 
-TOL = {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3}
-TOL_SMALL = {"fp32": 1e-6, "tc_fp16": 2e-3, "tc_bf16": 1.6e-2}
+TOL = {"fp32": 1e-6, "tc_fp16": 1e-4, "tc_bf16": 1e-3, "tc_fp16x3": 2e-5, "tc_bf16x3": 2e-5}
+TOL_SMALL = {"fp32": 1e-6, "tc_fp16": 2e-3, "tc_bf16": 1.6e-2, "tc_fp16x3": 2e-5, "tc_bf16x3": 2e-5}
 METHODS = [("exact", oracle.EXACT), ("uv", oracle.UV), ("img", oracle.IMG)]
 
 
@@ -66,7 +67,7 @@ def c1():
     return obs, batch, refs
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tc_fp16", "tc_bf16"])
+@pytest.mark.parametrize("prec", ["fp32", "tc_fp16", "tc_bf16", "tc_fp16x3", "tc_bf16x3"])
 @pytest.mark.parametrize("method", ["exact", "uv", "img"])
 def test_config1_full_parity(psf, c1, prec, method):
     obs, batch, refs = c1
@@ -94,7 +95,7 @@ def _edge_obs(kind):
     raise KeyError(kind)
 
 
-@pytest.mark.parametrize("prec", ["fp32", "tc_fp16"])
+@pytest.mark.parametrize("prec", ["fp32", "tc_fp16", "tc_bf16x3"])
 @pytest.mark.parametrize("kind", ["bda_uniform_channels", "unequal_channels", "single_sample_bins"])
 @pytest.mark.parametrize("flags", [0, oracle.WTERM])
 def test_edge_observations(psf, prec, kind, flags):
@@ -166,6 +167,10 @@ def test_empty_batch_and_bad_requests(psf):
     with psf.Plan(obs, prec="fp32") as plan:           # the FP32 path takes large cutouts
         out = plan.exact(psf.Batch([[0.01, 0.0]], [258], 1e-5))
         assert torch.isfinite(out).all()
+    with psf.Plan(obs, prec="tc_bf16x3", flags=psf.PSF_COMPLEX_OUT) as plan:   # split precision: real parts only
+        with pytest.raises(psf.PsfError) as ei:
+            plan.exact(psf.Batch([[0.01, 0.0]], [16], 1e-5))
+        assert ei.value.status == -4
 
 
 # ------------------------------------------------------------------ workload 2 (sampled, full size)
@@ -182,7 +187,7 @@ def c2():
     return obs, batch, sel, refs
 
 
-@pytest.mark.parametrize("prec", ["tc_fp16", "fp32"])
+@pytest.mark.parametrize("prec", ["tc_fp16", "fp32", "tc_bf16x3"])
 def test_config2_sampled_pixels(psf, c2, prec):
     """MeerKAT-shaped single 128 x 128 cutout at full size, in the launch
     configuration the benchmark times; the oracle evaluates sampled pixels one by one."""
