@@ -154,10 +154,19 @@ typedef struct {
 int psf_plan(const psf_obs_t *obs, const psf_opts_t *opts, psf_plan_t *out);
 
 /* Windowed averaging (Sect. 2.3, Eqs. 15-16): the normalised boxcar over a bin's raw
- * samples and an output channel's raw channels replaced by a window X_pqkr, for the
- * exact method (psf_exact, the batched form and psf_adjoint; Methods 1 and 2 keep their
- * boxcar models).  Host float32 arrays, read during the call, either may be NULL (boxcar
- * in that direction; both NULL restores the boxcar):
+ * samples and an output channel's raw channels replaced by a window X_pqkr.  The exact
+ * method averages the fringe with the window's weights; Methods 1 and 2 replace their two
+ * sincs (the transforms of the boxcar) by the window's transforms under their linear-phase
+ * models: with A = dPsi / 2 pi and B = dPhi / 2 pi the phase changes across the bin and the
+ * band,
+ *   T(A) = sum_s x_s exp(-2 pi i A tau_s) sinc_pi(A / n),  tau_s = (s - (n - 1)/2) / n
+ *   F(B) = sum_c y_c exp(-2 pi i B (nu_c - nu_r) / Dnu_r) sinc_pi(B dnu_c / Dnu_r)
+ * (raw sample s carrying its weight x_s over its own 1/n of the bin, raw channel c its
+ * weight y_c over its width), D = T F, complex for asymmetric windows; a direction
+ * without a window keeps its sinc.  Applies to psf_exact, psf_approx_uv, psf_approx_img,
+ * psf_approx_uv_img, psf_clean and psf_adjoint (not to the gridded form of
+ * psf_approx_img_grid, whose cells mix baselines).  Host float32 arrays, read during the
+ * call, either may be NULL (boxcar in that direction; both NULL restores the boxcar):
  *   time_window  per baseline b the tavg[b] weights of a bin's raw samples, in bin order,
  *                concatenated over the baselines (sum of tavg entries)
  *   chan_window  [nbl][favg]: per baseline the weights of an output channel's favg raw

@@ -15,6 +15,7 @@
  *     visibilities ................................... Eqs. 21-23
  *   - Method 1 (uv-plane) sinc x sinc decorrelation ... Eqs. 31-35
  *   - Method 2 (image-plane) circular-track model ..... Eqs. 38-44, Algorithm 1
+ *   - windowed averages (exact, Methods 1 and 2) ...... Eqs. 15-16
  *   - Method 2 gridded on the cutout's uv grid ........ Eq. 45, Algorithm 1
  *   - vector-Jacobian product of the PSF sum (adjoint)  chain rule on Eqs. 21-22
  *
@@ -163,10 +164,11 @@ static void or_direction(double l0, double m0, int flags, double L[3], double dL
 static double or_dot3(const double *a, const double *b) { return a[0] * b[0] + a[1] * b[1] + a[2] * b[2]; }
 
 /* Method 2 (Eqs. 38-44, Algorithm 1) at one uv point (u, v) [lambda] with time interval
- * dt and fractional bandwidth r = dnu / nu: D = sinc(dPsi/2) sinc(dPhi/2) and its
- * derivatives with respect to l0 and m0.  w is ignored. */
-static void or_img_decorr(double u, double v, double dt, double r, double l0, double m0, int flags,
-                          double *D, double *Dl, double *Dm) {
+ * dt and fractional bandwidth r = dnu / nu: the half phase changes over the bin,
+ * A = dPsi / (2 pi) from the circular-track rates (Eqs. 40-41) and B = dPhi / (2 pi)
+ * (Eqs. 42-43), and their derivatives with respect to l0 and m0.  w is ignored. */
+static void or_img_args(double u, double v, double dt, double r, double l0, double m0, int flags,
+                        double AB[6] /* A, dA/dl0, dA/dm0, B, dB/dl0, dB/dm0 */) {
     double uvlen = sqrt(u * u + v * v);
     double udot, vdot;   /* Eqs. 40-41 divided by omega_E */
     if (flags & OR_LITERAL_THETA) {
@@ -179,15 +181,82 @@ static void or_img_decorr(double u, double v, double dt, double r, double l0, do
         vdot = uvlen * cos(th);
     }
     double rho = sqrt(l0 * l0 + m0 * m0);
-    double A = OR_OMEGA_E * dt * (udot * l0 + vdot * m0);        /* dPsi / (2 pi) */
-    double B = r * uvlen * rho;                                 /* dPhi / (2 pi) */
-    double Al = OR_OMEGA_E * dt * udot, Am = OR_OMEGA_E * dt * vdot;
-    double Bl = rho > 0 ? r * uvlen * l0 / rho : 0.0;
-    double Bm = rho > 0 ? r * uvlen * m0 / rho : 0.0;
-    double sA = or_sincpi(A), sB = or_sincpi(B), dA = or_dsincpi(A), dB = or_dsincpi(B);
+    AB[0] = OR_OMEGA_E * dt * (udot * l0 + vdot * m0);        /* dPsi / (2 pi) */
+    AB[1] = OR_OMEGA_E * dt * udot;
+    AB[2] = OR_OMEGA_E * dt * vdot;
+    AB[3] = r * uvlen * rho;                                  /* dPhi / (2 pi) */
+    AB[4] = rho > 0 ? r * uvlen * l0 / rho : 0.0;
+    AB[5] = rho > 0 ? r * uvlen * m0 / rho : 0.0;
+}
+
+/* Method 2 with the boxcar: D = sinc(dPsi/2) sinc(dPhi/2) and its derivatives. */
+static void or_img_decorr(double u, double v, double dt, double r, double l0, double m0, int flags,
+                          double *D, double *Dl, double *Dm) {
+    double AB[6];
+    or_img_args(u, v, dt, r, l0, m0, flags, AB);
+    double sA = or_sincpi(AB[0]), sB = or_sincpi(AB[3]), dA = or_dsincpi(AB[0]), dB = or_dsincpi(AB[3]);
     *D = sA * sB;
-    *Dl = dA * Al * sB + sA * dB * Bl;
-    *Dm = dA * Am * sB + sA * dB * Bm;
+    *Dl = dA * AB[1] * sB + sA * dB * AB[4];
+    *Dm = dA * AB[2] * sB + sA * dB * AB[5];
+}
+
+/* Time factor of Methods 1 and 2 with A = dPsi / (2 pi), the phase change across the bin
+ * in turns: the bin average of exp(-2 pi i A tau), tau in [-1/2, 1/2] the time from the bin
+ * centre in bin lengths (Eq. 35's sinc(dPsi/2) for the boxcar).  With a time window
+ * (Eqs. 15-16) raw sample s of the n carries its normalised weight x_s over its own 1/n of
+ * the bin, centred at tau_s = (s - (n - 1)/2) / n, so the average is
+ *   T(A) = sum_s x_s exp(-2 pi i A tau_s) sinc_pi(A / n),
+ * which for x_s = 1/n is sinc_pi(A) again.  T and dT/dA as (re, im). */
+static void or_time_factor(const or_obs *o, const or_vis *x, double A, double T[2], double dT[2]) {
+    if (!o->twin) {
+        T[0] = or_sincpi(A); T[1] = 0;
+        dT[0] = or_dsincpi(A); dT[1] = 0;
+        return;
+    }
+    double tnorm = 0;
+    for (int s = 0; s < x->n; ++s) tnorm += o->twin[x->toff + s];
+    double Sr = 0, Si = 0, dSr = 0, dSi = 0;
+    for (int s = 0; s < x->n; ++s) {
+        double xs = o->twin[x->toff + s] / tnorm;
+        double tau = (s - 0.5 * (x->n - 1)) / x->n;
+        double ph = -2 * OR_PI * A * tau;                 /* exp(i ph) */
+        Sr += xs * cos(ph);
+        Si += xs * sin(ph);
+        /* d/dA exp(i ph) = -2 pi i tau exp(i ph) */
+        dSr += xs * 2 * OR_PI * tau * sin(ph);
+        dSi += -xs * 2 * OR_PI * tau * cos(ph);
+    }
+    double sc = or_sincpi(A / x->n), dsc = or_dsincpi(A / x->n) / x->n;
+    T[0] = sc * Sr; T[1] = sc * Si;
+    dT[0] = dsc * Sr + sc * dSr; dT[1] = dsc * Si + sc * dSi;
+}
+
+/* Frequency factor of Methods 1 and 2 with B = dPhi / (2 pi) over the output channel's band
+ * Dnu_r (Eq. 35's sinc(dPhi/2) for the boxcar).  With a channel window raw channel c (centre
+ * nu_c, width dnu_c) carries its normalised weight y_c (window x width) and its phase is
+ * integrated over its width, the phase across the band being linear in frequency:
+ *   F(B) = sum_c y_c exp(-2 pi i B (nu_c - nu_r) / Dnu_r) sinc_pi(B dnu_c / Dnu_r). */
+static void or_freq_factor(const or_obs *o, const or_vis *x, double B, double F[2], double dF[2]) {
+    if (!o->cwin) {
+        F[0] = or_sincpi(B); F[1] = 0;
+        dF[0] = or_dsincpi(B); dF[1] = 0;
+        return;
+    }
+    const int c0 = x->r * o->favg;
+    double cnorm = 0;
+    for (int c = c0; c < c0 + o->favg; ++c) cnorm += (double)o->cwin[(int64_t)x->b * o->favg + (c - c0)] * o->width[c];
+    F[0] = F[1] = dF[0] = dF[1] = 0;
+    for (int c = c0; c < c0 + o->favg; ++c) {
+        double yc = o->cwin[(int64_t)x->b * o->favg + (c - c0)] * o->width[c] / cnorm;
+        double nt = (o->freq[c] - x->nu) / x->dnu, om = o->width[c] / x->dnu;
+        double ph = -2 * OR_PI * B * nt;
+        double cs = cos(ph), sn = sin(ph), sc = or_sincpi(B * om), dsc = or_dsincpi(B * om) * om;
+        F[0] += yc * cs * sc;
+        F[1] += yc * sn * sc;
+        /* d/dB [exp(i ph) sc] = exp(i ph) (-2 pi i nt sc + dsc) */
+        dF[0] += yc * (cs * dsc + 2 * OR_PI * nt * sn * sc);
+        dF[1] += yc * (sn * dsc - 2 * OR_PI * nt * cs * sc);
+    }
 }
 
 /* Decorrelation D_k(l0) and its gradient, for one averaged visibility.
@@ -239,18 +308,36 @@ static void or_decorr_one(const or_obs *o, const or_vis *x, int method, double l
                 gm_im += f * (-2 * OR_PI * phm * cp * S + sp * dS * Xs_m);
             }
         }
-    } else if (method == 1) {
-        double A = or_dot3(x->dedge, L) * x->nu / OR_C_LIGHT;
-        double B = or_dot3(x->ubar, L) * x->dnu / OR_C_LIGHT;
-        double Al = or_dot3(x->dedge, dLl) * x->nu / OR_C_LIGHT, Am = or_dot3(x->dedge, dLm) * x->nu / OR_C_LIGHT;
-        double Bl = or_dot3(x->ubar, dLl) * x->dnu / OR_C_LIGHT, Bm = or_dot3(x->ubar, dLm) * x->dnu / OR_C_LIGHT;
-        double sA = or_sincpi(A), sB = or_sincpi(B), dA = or_dsincpi(A), dB = or_dsincpi(B);
-        re = sA * sB;
-        gl_re = dA * Al * sB + sA * dB * Bl;
-        gm_re = dA * Am * sB + sA * dB * Bm;
     } else {
-        double u = x->ubar[0] * x->nu / OR_C_LIGHT, v = x->ubar[1] * x->nu / OR_C_LIGHT;
-        or_img_decorr(u, v, x->dt, x->dnu / x->nu, l0, m0, flags, &re, &gl_re, &gm_re);
+        /* Methods 1 and 2: D = T(A) F(B), the time and frequency factors of the bin with the
+         * half phase changes A = dPsi / (2 pi) and B = dPhi / (2 pi):
+         *   Method 1 (Eqs. 31-35): A from the bin-edge uvw delta at nu_r, B from the bin
+         *   centre across the band Dnu_r;
+         *   Method 2 (Eqs. 38-44): A, B of the circular-track model at the visibility's uv. */
+        double AB[6];
+        if (method == 1) {
+            AB[0] = or_dot3(x->dedge, L) * x->nu / OR_C_LIGHT;
+            AB[1] = or_dot3(x->dedge, dLl) * x->nu / OR_C_LIGHT;
+            AB[2] = or_dot3(x->dedge, dLm) * x->nu / OR_C_LIGHT;
+            AB[3] = or_dot3(x->ubar, L) * x->dnu / OR_C_LIGHT;
+            AB[4] = or_dot3(x->ubar, dLl) * x->dnu / OR_C_LIGHT;
+            AB[5] = or_dot3(x->ubar, dLm) * x->dnu / OR_C_LIGHT;
+        } else {
+            double u = x->ubar[0] * x->nu / OR_C_LIGHT, v = x->ubar[1] * x->nu / OR_C_LIGHT;
+            or_img_args(u, v, x->dt, x->dnu / x->nu, l0, m0, flags, AB);
+        }
+        double T[2], dT[2], F[2], dF[2];
+        or_time_factor(o, x, AB[0], T, dT);
+        or_freq_factor(o, x, AB[3], F, dF);
+        re = T[0] * F[0] - T[1] * F[1];
+        im = T[0] * F[1] + T[1] * F[0];
+        /* dD = dT/dA dA F + T dF/dB dB */
+        for (int q = 0; q < 2; ++q) {
+            const double a = AB[1 + q], b = AB[4 + q];
+            const double gr = a * (dT[0] * F[0] - dT[1] * F[1]) + b * (T[0] * dF[0] - T[1] * dF[1]);
+            const double gi = a * (dT[0] * F[1] + dT[1] * F[0]) + b * (T[0] * dF[1] + T[1] * dF[0]);
+            if (q == 0) { gl_re = gr; gl_im = gi; } else { gm_re = gr; gm_im = gi; }
+        }
     }
     *Dre = re; *Dim = im;
     if (g) { g[0] = gl_re; g[1] = gl_im; g[2] = gm_re; g[3] = gm_im; }

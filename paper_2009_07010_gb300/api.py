@@ -94,9 +94,9 @@ class Plan:
             self.set_windows(tw, cw)
 
     def set_windows(self, time_window=None, chan_window=None):
-        """Windowed averaging of the exact method (Eqs. 15-16): per-baseline weights over a
-        bin's raw samples (concatenated over baselines) and [nbl, favg] over an output
-        channel's raw channels; None for the boxcar."""
+        """Windowed averaging (Eqs. 15-16) for the exact method and Methods 1 and 2:
+        per-baseline weights over a bin's raw samples (concatenated over baselines) and
+        [nbl, favg] over an output channel's raw channels; None for the boxcar."""
         tw = None if time_window is None else np.ascontiguousarray(time_window, np.float32)
         cw = None if chan_window is None else np.ascontiguousarray(chan_window, np.float32)
         check(_lib.lib().psf_plan_set_windows(self._h, None if tw is None else ctypes.c_void_p(tw.ctypes.data),

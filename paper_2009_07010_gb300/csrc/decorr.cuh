@@ -190,7 +190,86 @@ __device__ __forceinline__ float2 decorr_exact(const DevObs &o, int bin, int r, 
     return make_float2(re * inv, im * inv);
 }
 
-// Method 1 (Eqs. 31-35): sinc_pi(dedge.L0 nu_r / c) * sinc_pi(ubar.L0 Dnu_r / c).
+// Windowed time factor of Methods 1 and 2 (Eqs. 15-16 with the linear phase of the
+// approximations): with A the phase change across the bin in turns, the bin average of
+// exp(-2 pi i A tau), tau in [-1/2, 1/2] the time from the bin centre in bin lengths, when
+// raw sample s of the n carries its normalised weight x_s over its own 1/n of the bin:
+//   T(A) = sum_s x_s exp(-2 pi i A tau_s) sinc_pi(A / n),  tau_s = (s - (n - 1)/2) / n
+// (sinc_pi(A) for x_s = 1/n).  dT: dT/dA.
+template <bool GRAD, bool FAST>
+__device__ __forceinline__ float2 win_time(const DevObs &o, int2 sm, float A, float2 *dT) {
+    const float n = (float)sm.y;
+    float sr = 0.f, si = 0.f, dr = 0.f, di = 0.f;
+    for (int s = 0; s < sm.y; ++s) {
+        const float xs = o.samp_w[sm.x + s];
+        const float tau = ((float)s - 0.5f * (n - 1.0f)) / n;
+        float sn, cs;
+        sincospi2_t<FAST>(-A * tau, &sn, &cs);   // exp(-2 pi i A tau)
+        sr += xs * cs;
+        si += xs * sn;
+        if (GRAD) {   // d/dA exp(-2 pi i A tau) = -2 pi i tau exp(...), the 2 pi applied below
+            dr += xs * tau * sn;
+            di -= xs * tau * cs;
+        }
+    }
+    const float sc = sincpi_t<FAST>(A / n);
+    if (GRAD) {
+        const float dsc = dsincpi(A / n) / n;
+        *dT = make_float2(dsc * sr + 2.0f * kPiF * sc * dr, dsc * si + 2.0f * kPiF * sc * di);
+    }
+    return make_float2(sc * sr, sc * si);
+}
+
+// Windowed frequency factor: with B the phase change across the output channel's band
+// Dnu_r in turns, raw channel c (offset nu_c - nu_r, width dnu_c) carrying its normalised
+// weight y_c (window x width) with its phase integrated over its width:
+//   F(B) = sum_c y_c exp(-2 pi i B (nu_c - nu_r) / Dnu_r) sinc_pi(B dnu_c / Dnu_r).
+template <bool GRAD, bool FAST>
+__device__ __forceinline__ float2 win_freq(const DevObs &o, int bin, int r, float B, float2 *dF) {
+    const float Dnu = o.chan[r].y;
+    const float *cw = o.chan_win + (int64_t)o.bin_bl[bin] * (o.nout * o.favg) + (int64_t)r * o.favg;
+    float fr = 0.f, fi = 0.f, dr = 0.f, di = 0.f;
+    for (int c = 0; c < o.favg; ++c) {
+        const float4 rc = o.rawchan[r * o.favg + c];
+        const float yc = cw[c];
+        const float nt = rc.x / Dnu, om = rc.z;
+        float sn, cs;
+        sincospi2_t<FAST>(-B * nt, &sn, &cs);
+        const float sc = sincpi_t<FAST>(B * om);
+        fr += yc * cs * sc;
+        fi += yc * sn * sc;
+        if (GRAD) {   // d/dB [exp(-2 pi i B nt) sc] = exp(...) (dsc - 2 pi i nt sc)
+            const float dsc = dsincpi(B * om) * om;
+            dr += yc * (cs * dsc + 2.0f * kPiF * nt * sn * sc);
+            di += yc * (sn * dsc - 2.0f * kPiF * nt * cs * sc);
+        }
+    }
+    if (GRAD) *dF = make_float2(dr, di);
+    return make_float2(fr, fi);
+}
+
+// D = T(A) F(B) of a windowed approximation (win: bit 0 a time window, bit 1 a channel
+// window; the direction without a window keeps the boxcar's sinc_pi), with the gradient
+// from dA/dl0, dA/dm0, dB/dl0, dB/dm0.
+template <bool GRAD, bool FAST>
+__device__ __forceinline__ float2 decorr_windowed(const DevObs &o, int bin, int r, float A, float B, float Al,
+                                                  float Am, float Bl, float Bm, float4 *grad) {
+    float2 dT = make_float2(0.f, 0.f), dF = make_float2(0.f, 0.f);
+    const float2 T = (o.win & 1) ? win_time<GRAD, FAST>(o, o.bin_samp[bin], A, &dT)
+                                 : make_float2(sincpi_t<FAST>(A), 0.f);
+    const float2 F = (o.win & 2) ? win_freq<GRAD, FAST>(o, bin, r, B, &dF) : make_float2(sincpi_t<FAST>(B), 0.f);
+    if (GRAD) {
+        if (!(o.win & 1)) dT = make_float2(dsincpi(A), 0.f);
+        if (!(o.win & 2)) dF = make_float2(dsincpi(B), 0.f);
+        const float2 tF = make_float2(dT.x * F.x - dT.y * F.y, dT.x * F.y + dT.y * F.x);   // dT F
+        const float2 Tf = make_float2(T.x * dF.x - T.y * dF.y, T.x * dF.y + T.y * dF.x);   // T dF
+        *grad = make_float4(Al * tF.x + Bl * Tf.x, Al * tF.y + Bl * Tf.y, Am * tF.x + Bm * Tf.x, Am * tF.y + Bm * Tf.y);
+    }
+    return make_float2(T.x * F.x - T.y * F.y, T.x * F.y + T.y * F.x);
+}
+
+// Method 1 (Eqs. 31-35): sinc_pi(dedge.L0 nu_r / c) * sinc_pi(ubar.L0 Dnu_r / c); with
+// windows the window transforms T, F above in place of the two sincs.
 template <bool GRAD, bool FAST = false>
 __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, float4 L, float4 dLl,
                                             float4 dLm, float4 *grad) {
@@ -199,6 +278,14 @@ __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, flo
     const float4 ch = o.chan[r];
     const float A = dot3(ed, L) * ch.x * kInvC;
     const float B = dot3(ub, L) * ch.y * kInvC;
+    if (o.win) {
+        float Al = 0.f, Am = 0.f, Bl = 0.f, Bm = 0.f;
+        if (GRAD) {
+            Al = dot3(ed, dLl) * ch.x * kInvC; Am = dot3(ed, dLm) * ch.x * kInvC;
+            Bl = dot3(ub, dLl) * ch.y * kInvC; Bm = dot3(ub, dLm) * ch.y * kInvC;
+        }
+        return decorr_windowed<GRAD, FAST>(o, bin, r, A, B, Al, Am, Bl, Bm, grad);
+    }
     const float sA = sincpi_t<FAST>(A), sB = sincpi_t<FAST>(B);
     if (GRAD) {
         const float dA = dsincpi(A), dB = dsincpi(B);
@@ -209,7 +296,8 @@ __device__ __forceinline__ float2 decorr_uv(const DevObs &o, int bin, int r, flo
     return make_float2(sA * sB, 0.0f);
 }
 
-// Method 2 (Eqs. 38-44, Algorithm 1 at the visibility's own uv point):
+// Method 2 (Eqs. 38-44, Algorithm 1 at the visibility's own uv point; with windows the
+// window transforms in place of the two sincs):
 //   (du/dt, dv/dt) = omega_E (-v, u) for theta = atan2(v, u), or the literal
 //   arctan(u/v) reading when PSF_IMG_LITERAL_THETA is set;
 //   D = sinc_pi(omega_E Dt (udot l0 + vdot m0)) sinc_pi((Dnu/nu) |u| |l0|).
@@ -234,6 +322,10 @@ __device__ __forceinline__ float2 decorr_img(const DevObs &o, int bin, int r, fl
     const float fb = ch.y / ch.x * uvlen;
     const float A = wdt * (udot * L.x + vdot * L.y);
     const float B = fb * rho;
+    if (o.win) {
+        const float Bl = rho > 0.f ? fb * L.x / rho : 0.f, Bm = rho > 0.f ? fb * L.y / rho : 0.f;
+        return decorr_windowed<GRAD, FAST>(o, bin, r, A, B, wdt * udot, wdt * vdot, Bl, Bm, grad);
+    }
     const float sA = sincpi_t<FAST>(A), sB = sincpi_t<FAST>(B);
     if (GRAD) {
         const float dA = dsincpi(A), dB = dsincpi(B);

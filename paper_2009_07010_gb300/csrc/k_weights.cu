@@ -281,7 +281,7 @@ cudaError_t launch_weights16(const DevObs &o, int method, uint32_t flags, const 
         return cudaGetLastError();
     }
     const unsigned gy = (unsigned)((rows + kRowsPerBlock - 1) / kRowsPerBlock);
-    if (method != kExact) {   // real weights: kpitch pairs per row hold 2 kpitch visibilities
+    if (method != kExact && !o.win) {   // real weights: kpitch pairs per row hold 2 kpitch visibilities
         const int64_t kp2 = kpitch / 2;
         dim3 grid((unsigned)((kp2 + 255) / 256), gy);
         if (bf16)

@@ -437,7 +437,7 @@ int psf_plan_set_windows(psf_plan_t p, const float *tw, const float *cw) {
     d.samp_w = (const float *)p->samp_w.p;
     d.chan_win = (const float *)p->chan_win.p;
     d.bin_bl = (const int32_t *)p->bin_bl.p;
-    d.win = 1;
+    d.win = (tw ? 1 : 0) | (cw ? 2 : 0);
     d.chan_affine = 0;   // the channel recurrence of the exact weights assumes the boxcar
     return PSF_OK;
 }
@@ -560,9 +560,9 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
     const int rows = ntile * 128;
     const int64_t K = p->nvis;
     const int bf16 = prec_bf16(p->opts.prec);
-    // Methods 1 and 2 have real weights: one K' column per visibility, 64-visibility
-    // stages; the exact method has complex weights: two columns, 32-visibility stages.
-    const int real = method != kExact;
+    // Methods 1 and 2 have real weights (unless windowed): one K' column per visibility,
+    // 64-visibility stages; complex weights: two columns, 32-visibility stages.
+    const int real = method != kExact && p->d.win == 0;
     const int64_t ks = real ? 64 : 32;
     const size_t bytes_per = real ? 2 : 4;
     int64_t KC = (int64_t)(kW16Budget / ((size_t)rows * bytes_per)) / 64 * 64;
@@ -815,7 +815,9 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
             PSF_TRY(launch_psf_fp32(p->d, w, ldw, (const Tile *)(dm + m.off_tiles), (int)tiles.size(), nsplit,
                                     kper, h.cell, part, stride, st));
         } else {
-            int wreal = method != PSF_METHOD_EXACT ? 1 : 0;
+            // the approximations' weights are real unless windowed (Eqs. 15-16: a window's
+            // transform is complex in general)
+            int wreal = (method != PSF_METHOD_EXACT && p->d.win == 0) ? 1 : 0;
             if (wreal) {
                 bool whole = true;
                 for (const auto &t : items)
@@ -852,7 +854,7 @@ int run_forward_uvimg(psf_plan_s *p, const psf_batch_t *b, float *out_uv, float 
     BatchHost h;
     int s = prepare_batch(p, b, h, tc ? 256 : 4096);
     if (s || h.npos == 0) return s;
-    bool fused = tc;
+    bool fused = tc && p->d.win == 0;   // the fused pass needs real weights
     int n64 = 0, n128 = 0;
     for (int i = 0; i < h.npos && fused; ++i) {
         if (h.npix[i] == 64) ++n64;

@@ -32,7 +32,9 @@ struct DevObs {
     const float *W;           // [nvis] visibility weights
     const float2 *uv;         // [nvis] bin-centre (u, v) in wavelengths, rounded to float32
     const float2 *uv_lo;      // [nvis] (u, v) - uv: the float64 bin centre is uv + uv_lo
-    // windowed average (Eqs. 15-16), exact method; win = 0: the boxcar
+    // windowed average (Eqs. 15-16); win = 0: the boxcar; bit 0: a time window was given,
+    // bit 1: a channel window (the exact method reads both tables whenever win != 0, the
+    // approximations take the transform of the given window in each direction)
     int32_t win;
     const float *samp_w;      // [nsamp] normalised time weight of each raw-sample record
     const float *chan_win;    // [nbl][nchan] normalised channel weight (window x width)
