@@ -298,17 +298,33 @@ def measure_batched(psf, prec, steps=2, which="c4"):
         total_ms += ms_m
     ms = total_ms
     adj = None
-    if which == "c4":   # adjoint of the exact method (FP32 CUDA cores)
+    if which == "c4":   # adjoint of the exact method: tensor cores (the plan's precision) and FP32
         R = torch.randn(batch.total(), device="cuda", generator=torch.Generator(device="cuda").manual_seed(1))
-        plan.adjoint("exact", batch, R)
-        torch.cuda.synchronize()
-        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a0.record()
-        plan.adjoint("exact", batch, R)
-        a1.record()
-        torch.cuda.synchronize()
-        ams = a0.elapsed_time(a1)
-        adj = {"ms": ams, "terms_per_s": K * bg.total_pixels() / (ams * 1e-3), "precision": "fp32"}
+        adj = {}
+        for ap in (prec, "fp32"):
+            plan.set_opts(prec=ap)
+            plan.adjoint("exact", batch, R)
+            torch.cuda.synchronize()
+            plan.profile_read()
+            plan.profile_enable(True)
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record()
+            plan.adjoint("exact", batch, R)
+            a1.record()
+            torch.cuda.synchronize()
+            kms, nkc, _ = plan.profile_read()
+            plan.profile_enable(False)
+            ams = a0.elapsed_time(a1)
+            tc = ap in ("tc_fp16", "tc_bf16")
+            adj[ap] = {"ms": ams, "terms_per_s": K * bg.total_pixels() / (ams * 1e-3),
+                       "form": "tensor-core H (k_adj_tc) + FP32 decorrelation gradients (k_adj_fold)" if tc
+                       else "FP32 CUDA cores (k_adjoint)"}
+            if tc:   # 4 algorithmic flops per (position, pixel, visibility) of H
+                adj[ap]["tc_kernel_ms"] = kms
+                adj[ap]["tc_kernel_tflops"] = 4.0 * K * bg.total_pixels() / (kms * 1e-3) / 1e12
+                adj[ap]["tc_kernel_frac_of_peak"] = adj[ap]["tc_kernel_tflops"] / peaks["bf16_tflops"]
+        plan.set_opts(prec=prec)
+        adj["speedup_tc_over_fp32"] = adj["fp32"]["ms"] / adj[prec]["ms"] if prec in adj and prec != "fp32" else None
     st = plan.sync_status()
     plan.close()
     if st != 0:

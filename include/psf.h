@@ -178,6 +178,13 @@ int psf_plan(const psf_obs_t *obs, const psf_opts_t *opts, psf_plan_t *out);
  * PSF_ENOMEM / PSF_ECUDA on allocation or copy failure. */
 int psf_plan_set_windows(psf_plan_t plan, const float *time_window, const float *chan_window);
 
+/* Replace the visibility weights W_k (Eq. 6) used by later calls on this plan:
+ * weights_dev is a device float32 [nvis] array in plan order, copied on cuda_stream
+ * (stream-ordered: the array may be released once the stream has passed the call), or
+ * NULL for the natural weights W_k = tavg[b] * favg.  Errors: PSF_EINVAL (NULL plan),
+ * PSF_ECUDA (copy failure). */
+int psf_plan_set_weights(psf_plan_t plan, const float *weights_dev, void *cuda_stream);
+
 /* Replace the precision / flags / algorithm used by later calls on this plan. */
 int psf_plan_set_opts(psf_plan_t plan, const psf_opts_t *opts);
 
@@ -296,7 +303,15 @@ int psf_fwhm(psf_plan_t plan, const psf_batch_t *batch, const float *cutouts_dev
  * writes dL/d(l0,m0) to dL_dlm_dev (device float64 [npos][2], overwritten) and,
  * if dL_dW_dev is not NULL, dL/dW_k summed over positions (device float32 [nvis],
  * overwritten).  The position enters only through D_k (the twiddles depend on the
- * pixel offsets only).  Always evaluated in FP32. */
+ * pixel offsets only):
+ *   H_pk = sum_ij dL/dP_p[j][i] exp(2 pi i (u_k dl_i + v_k dm_j)),
+ *   dL/dW_k = sum_p Re(D_k(l0_p) H_pk),  dL/dl0_p = sum_k W_k Re(dD_k/dl0 H_pk).
+ * Precision: plans in PSF_TC_FP16 / PSF_TC_BF16 whose cutouts are all multiples of 32
+ * pixels (up to 1024) form H on the tensor cores (dL/dP and the twiddles rounded to the
+ * plan's 16-bit type, FP32 accumulation; about 3e-4 (FP16) / 3e-3 (BF16) of the largest
+ * gradient component) and D with its gradient in FP32 with the MUFU sine/cosine; every
+ * other plan (PSF_FP32, the split modes, other sizes, N <= 512) runs the FP32 CUDA-core
+ * adjoint (about 1e-6). */
 int psf_adjoint(psf_plan_t plan, int method, const psf_batch_t *batch, const float *dL_dP_dev,
                 double *dL_dlm_dev, float *dL_dW_dev, void *cuda_stream);
 

@@ -19,7 +19,7 @@ PSF_ALGO_AUTO, PSF_ALGO_CUTOUT = 0, 1
 EXACT, UV, IMG, IMG_GRID = 0, 1, 2, 3
 
 # every function include/psf.h declares
-EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_set_windows", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
+EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_set_windows", "psf_plan_set_weights", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
            "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_clean", "psf_fwhm", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
            "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
 
@@ -79,6 +79,8 @@ def lib(auto_build: bool = False):
             L.psf_plan_set_opts.restype = I
             L.psf_plan_set_windows.argtypes = [P, P, P]
             L.psf_plan_set_windows.restype = I
+            L.psf_plan_set_weights.argtypes = [P, P, P]
+            L.psf_plan_set_weights.restype = I
             L.psf_plan_nvis.argtypes = [P]
             L.psf_plan_nvis.restype = ctypes.c_int64
             for name in ("psf_exact", "psf_approx_uv", "psf_approx_img", "psf_approx_img_grid"):

@@ -103,6 +103,14 @@ class Plan:
                                               None if cw is None else ctypes.c_void_p(cw.ctypes.data)),
               "psf_plan_set_windows")
 
+    def set_weights(self, W: Optional[torch.Tensor] = None, stream=None):
+        """Visibility weights W_k (device float32 [nvis], plan order) for later calls;
+        None restores the natural weights."""
+        if W is not None:
+            assert W.dtype == torch.float32 and W.is_cuda and W.is_contiguous() and W.numel() == self.nvis
+        check(_lib.lib().psf_plan_set_weights(self._h, None if W is None else ctypes.c_void_p(W.data_ptr()),
+                                              _stream_handle(stream)), "psf_plan_set_weights")
+
     def set_opts(self, prec: Optional[str] = None, flags: Optional[int] = None, algo: Optional[int] = None):
         self.prec = prec if prec is not None else self.prec
         self.flags = flags if flags is not None else self.flags
@@ -251,28 +259,40 @@ def selftest_umma(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
 
 
 class SmearedPSF(torch.autograd.Function):
-    """Cutouts as a differentiable function of the positions (l0, m0).
+    """Cutouts as a differentiable function of the positions (l0, m0) and, optionally,
+    of the visibility weights W_k.
 
-    forward(lm) evaluates `method` on the plan's observation; backward runs the
-    library's adjoint (psf_adjoint) on the incoming gradient.  lm is a float64 host
-    tensor [npos, 2] (positions are host inputs of the C ABI); the returned gradient
-    lives on the same device as lm.
+    forward(lm, W, ...) evaluates `method` on the plan's observation in the plan's
+    precision (with W given, the plan's weights are replaced by W first and stay so);
+    backward runs the library's adjoint (psf_adjoint) on the incoming gradient.  The
+    backward is the vector-Jacobian product of the exact map of Eqs. 21-22 (the FP64
+    definition), not of the rounded forward: FP32 CUDA cores for PSF_FP32 and the split
+    precision plans (about 1e-6 of the largest gradient component), the tensor-core
+    adjoint (H in FP16/BF16 operands, FP32 accumulation; about 3e-4 / 3e-3) for
+    single-pass FP16/BF16 plans whose cutouts are multiples of 32 pixels.  lm is a
+    float64 host tensor [npos, 2] (positions are host inputs of the C ABI), its gradient
+    is returned on lm's device; W is a device float32 tensor [nvis] or None.
     """
 
     @staticmethod
-    def forward(ctx, lm, plan, method, npix, cell):
+    def forward(ctx, lm, W, plan, method, npix, cell):
         batch = Batch(lm.detach().cpu().numpy(), npix, cell)
+        if W is not None:
+            plan.set_weights(W.detach().contiguous())
         out = plan.forward(method, batch)[:batch.total()]
         ctx.plan, ctx.method, ctx.batch, ctx.lm_device = plan, method, batch, lm.device
+        ctx.want_W = W is not None
         return out
 
     @staticmethod
     def backward(ctx, grad_out):
         g = grad_out.detach().to(torch.float32).contiguous()
-        g_lm, _ = ctx.plan.adjoint(ctx.method, ctx.batch, g, want_dW=False)
-        return g_lm.to(ctx.lm_device), None, None, None, None
+        g_lm, g_W = ctx.plan.adjoint(ctx.method, ctx.batch, g, want_dW=ctx.want_W and ctx.needs_input_grad[1])
+        return g_lm.to(ctx.lm_device), g_W, None, None, None, None
 
 
-def smeared_psf(plan: Plan, method: str, lm: torch.Tensor, npix, cell: float) -> torch.Tensor:
-    """Differentiable cutouts of `method` at positions lm (see SmearedPSF)."""
-    return SmearedPSF.apply(lm, plan, method, npix, cell)
+def smeared_psf(plan: Plan, method: str, lm: torch.Tensor, npix, cell: float,
+                W: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Differentiable cutouts of `method` at positions lm, optionally with weights W
+    (see SmearedPSF)."""
+    return SmearedPSF.apply(lm, W, plan, method, npix, cell)

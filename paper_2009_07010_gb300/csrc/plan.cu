@@ -442,6 +442,18 @@ int psf_plan_set_windows(psf_plan_t p, const float *tw, const float *cw) {
     return PSF_OK;
 }
 
+int psf_plan_set_weights(psf_plan_t p, const float *w, void *stream) {
+    if (!p) return PSF_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (w) {
+        PSF_TRY(cudaMemcpyAsync(p->W.p, w, (size_t)p->nvis * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        return PSF_OK;
+    }
+    PSF_TRY(launch_fill_vis(p->d, (const double2 *)p->bin_uv64.p, (const double2 *)p->chan64.p, (float2 *)p->uv.p,
+                            (float2 *)p->uv_lo.p, (float *)p->W.p, 1, st));
+    return PSF_OK;
+}
+
 int psf_plan_set_opts(psf_plan_t p, const psf_opts_t *opts) {
     if (!p || !opts) return PSF_EINVAL;
     int st = validate_opts(opts);
@@ -1277,6 +1289,107 @@ int run_clean(psf_plan_s *p, const psf_clean_t *c, float *res, float *model, int
 
 }  // namespace
 
+namespace {
+
+struct AdjPosHost {
+    float4 L, dLl, dLm;
+};
+
+AdjPosHost adj_pos(const psf_plan_s *p, const BatchHost &h, const psf_batch_t *b, int i) {
+    const double l0 = b->lm[2 * i], m0 = b->lm[2 * i + 1];
+    float dzl = 0.f, dzm = 0.f;
+    if (p->opts.flags & PSF_WTERM) {   // d(n0 - 1)/dl0 = -l0 / n0
+        const double n0 = std::sqrt(1.0 - l0 * l0 - m0 * m0);
+        dzl = (float)(-l0 / n0);
+        dzm = (float)(-m0 / n0);
+    }
+    AdjPosHost a;
+    a.L = h.pos[i];
+    a.dLl = make_float4(1.f, 0.f, dzl, 0.f);
+    a.dLm = make_float4(0.f, 1.f, dzm, 0.f);
+    return a;
+}
+
+constexpr size_t kAdjHBudget = size_t(4) << 30;   // H of one visibility chunk (bytes)
+
+// Tensor-core adjoint (single-pass FP16/BF16 plans, cutouts of a multiple of 32 pixels):
+// per size group and chunk of at most adj_fold_max_pos() positions, R as 16-bit rows, H by
+// tcgen05 per visibility chunk, then the decorrelation gradients and the reductions.
+int run_adjoint_tc(psf_plan_s *p, int method, const psf_batch_t *b, const BatchHost &h, const float *dLdP,
+                   double *dLdlm, float *dLdW, cudaStream_t st) {
+    const int64_t K = p->nvis;
+    const int bf16 = prec_bf16(p->opts.prec);
+    std::vector<std::vector<int>> groups(1025);
+    for (int i = 0; i < h.npos; ++i) groups[h.npix[i]].push_back(i);
+    bool wrote_W = false;
+    for (int N = 32; N <= 1024; N += 32) {
+        const std::vector<int> &g = groups[N];
+        for (size_t c0 = 0; c0 < g.size(); c0 += (size_t)adj_fold_max_pos()) {
+            const int np = (int)std::min<size_t>(g.size() - c0, (size_t)adj_fold_max_pos());
+            const int rows = (np + 127) / 128 * 128;
+            const int64_t n2 = (int64_t)N * N;
+            std::vector<AdjPosHost> ap(np);
+            std::vector<int64_t> offs(np);
+            std::vector<int32_t> idx(np);
+            for (int q = 0; q < np; ++q) {
+                const int i = g[c0 + q];
+                ap[q] = adj_pos(p, h, b, i);
+                offs[q] = h.out_off[i];
+                idx[q] = i;
+            }
+            const size_t off_pos = 0;
+            const size_t off_offs = align_up(off_pos + np * sizeof(AdjPosHost), 16);
+            const size_t off_idx = align_up(off_offs + np * sizeof(int64_t), 16);
+            const size_t bytes = align_up(off_idx + np * sizeof(int32_t), 16);
+            std::vector<char> blob(bytes, 0);
+            std::memcpy(blob.data() + off_pos, ap.data(), np * sizeof(AdjPosHost));
+            std::memcpy(blob.data() + off_offs, offs.data(), np * sizeof(int64_t));
+            std::memcpy(blob.data() + off_idx, idx.data(), np * sizeof(int32_t));
+            int s = upload_meta(p, blob.data(), bytes, st);
+            if (s) return s;
+            char *dm = (char *)p->meta.p;
+            PSF_TRY(p->w16.reserve((size_t)rows * n2 * 2));
+            PSF_TRY(launch_adj_r16(dLdP, (const int64_t *)(dm + off_offs), np, rows, (int)n2, bf16, p->w16.p, st));
+            CUtensorMapStub rmap;
+            if ((s = make_weight_map(&rmap, p->w16.p, bf16, n2, rows))) return s;
+            int64_t Kc = (int64_t)(kAdjHBudget / ((size_t)rows * sizeof(float2))) / 128 * 128;
+            Kc = std::max<int64_t>(128, std::min<int64_t>(Kc, (K + 127) / 128 * 128));
+            const int64_t ldh = Kc;
+            PSF_TRY(p->wbuf.reserve((size_t)rows * ldh * sizeof(float2)));
+            PSF_TRY(p->partial.reserve((size_t)adj_fold_blocks(p->nsm) * np * 2 * sizeof(double)));
+            for (int64_t kc0 = 0; kc0 < K; kc0 += Kc) {
+                const int64_t kcn = std::min<int64_t>(Kc, K - kc0);
+                cudaEvent_t ev1 = nullptr, ev2 = nullptr;
+                if (p->prof) {
+                    if (p->prof_used == p->prof_ev.size()) {
+                        cudaEvent_t a, e2;
+                        PSF_TRY(cudaEventCreate(&a));
+                        PSF_TRY(cudaEventCreate(&e2));
+                        p->prof_ev.emplace_back(a, e2);
+                    }
+                    ev1 = p->prof_ev[p->prof_used].first;
+                    ev2 = p->prof_ev[p->prof_used].second;
+                    p->prof_used++;
+                    PSF_TRY(cudaEventRecord(ev1, st));
+                }
+                PSF_TRY(launch_adj_tc(&rmap, rows / 128, (int)((kcn + 127) / 128), N, p->d.uv, (int32_t)kc0,
+                                      (int32_t)kcn, (float)h.cell, (float2 *)p->wbuf.p, ldh, bf16, p->nsm,
+                                      (int *)p->err.p, st));
+                if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
+                p->n_contract++;
+                PSF_TRY(launch_adj_fold(p->d, method, p->opts.flags, dm + off_pos, np, (const float2 *)p->wbuf.p, ldh,
+                                        (int32_t)kc0, (int32_t)kcn, dLdW, wrote_W ? 1 : 0, (double *)p->partial.p,
+                                        (const int32_t *)(dm + off_idx), dLdlm, kc0 > 0 ? 1 : 0, 1, p->nsm, st));
+                p->n_kernels += 4;
+            }
+            wrote_W = dLdW != nullptr;
+        }
+    }
+    return PSF_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 int psf_approx_img_grid(psf_plan_t p, const psf_batch_t *b, float *out, void *stream) {
@@ -1342,32 +1455,33 @@ int psf_adjoint(psf_plan_t p, int method, const psf_batch_t *b, const float *dLd
     if (!p || !dLdP || !dLdlm) return PSF_EINVAL;
     if (method < 0 || method > 2) return PSF_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
+    // the tensor-core adjoint takes single-pass FP16/BF16 plans whose cutouts are all
+    // multiples of 32 pixels (up to 1024); the FP32 CUDA-core adjoint everything else
+    const bool tc1 = p->opts.prec == PSF_TC_FP16 || p->opts.prec == PSF_TC_BF16;
     BatchHost h;
-    int s = prepare_batch(p, b, h, adjoint_max_n());
+    int s = prepare_batch(p, b, h, tc1 ? 1024 : adjoint_max_n());
     if (s) return s;
     if (h.npos == 0) {
         if (dLdW) PSF_TRY(cudaMemsetAsync(dLdW, 0, p->nvis * sizeof(float), st));
         return PSF_OK;
     }
+    bool use_tc = tc1;
+    int nmax_all = 0;
+    for (int i = 0; i < h.npos; ++i) {
+        use_tc = use_tc && h.npix[i] % 32 == 0;
+        nmax_all = std::max(nmax_all, (int)h.npix[i]);
+    }
+    if (use_tc) return run_adjoint_tc(p, method, b, h, dLdP, dLdlm, dLdW, st);
+    if (nmax_all > adjoint_max_n()) return PSF_EUNSUPPORTED;
     const int64_t ncta = adjoint_ctas(p->nvis);
     const int64_t budget = int64_t(512) << 20;
     const int chunk = (int)std::max<int64_t>(1, std::min<int64_t>(h.npos, budget / (ncta * 16)));
-    struct AdjPosHost { float4 L, dLl, dLm; };
     for (int c0 = 0; c0 < h.npos; c0 += chunk) {
         const int cn = std::min(chunk, h.npos - c0);
         int nmax = 2;
         std::vector<AdjPosHost> ap(cn);
         for (int i = 0; i < cn; ++i) {
-            const double l0 = b->lm[2 * (c0 + i)], m0 = b->lm[2 * (c0 + i) + 1];
-            float dzl = 0.f, dzm = 0.f;
-            if (p->opts.flags & PSF_WTERM) {   // d(n0 - 1)/dl0 = -l0 / n0
-                const double n0 = std::sqrt(1.0 - l0 * l0 - m0 * m0);
-                dzl = (float)(-l0 / n0);
-                dzm = (float)(-m0 / n0);
-            }
-            ap[i].L = h.pos[c0 + i];
-            ap[i].dLl = make_float4(1.f, 0.f, dzl, 0.f);
-            ap[i].dLm = make_float4(0.f, 1.f, dzm, 0.f);
+            ap[i] = adj_pos(p, h, b, c0 + i);
             nmax = std::max(nmax, (int)h.npix[c0 + i]);
         }
         const size_t off_pos = 0;

@@ -81,6 +81,24 @@ cudaError_t launch_adjoint_chunk(const DevObs &o, int method, uint32_t flags, co
                                  const int64_t *offs, int npos, int nmax, double cell, const float *R, float *gW,
                                  int accumulate_gW, double *partial, double *g_lm, cudaStream_t st);
 
+// ---- tensor-core adjoint (k_adj_tc.cu) ------------------------------------
+// R of a size group (packed cutouts at offs[row], rows < npos) -> FP16/BF16 [rows][n2].
+cudaError_t launch_adj_r16(const float *R, const int64_t *offs, int npos, int rows, int n2, int bf16, void *r16,
+                           cudaStream_t st);
+// H[row][k - kc0] = sum_q R[row][q] exp(2 pi i (u_k dl_i + v_k dm_j)) for the visibility
+// chunk [kc0, kc0 + kcn) (float2 rows of ldh >= 128 ceil(kcn / 128)); rmap: the 2-D tensor
+// map of the R rows (make_weight_map with pitch n2 = N^2); N a multiple of 32.
+cudaError_t launch_adj_tc(const void *rmap, int ntile_pos, int ntile_vis, int N, const float2 *uv, int32_t kc0,
+                          int32_t kcn, float cell, float2 *H, int64_t ldh, int bf16, int nsm, int *err,
+                          cudaStream_t st);
+int adj_fold_max_pos();
+int adj_fold_blocks(int nsm);
+// From H of the chunk: gW[k] (+)= sum_p Re(D H) and g_lm[2 idx[p] + d] (+)= sum_k W Re(dD H);
+// pos: [npos] {L, dL/dl0, dL/dm0} float4 triples; partial: [adj_fold_blocks(nsm)][npos][2].
+cudaError_t launch_adj_fold(const DevObs &o, int method, uint32_t flags, const void *pos, int npos, const float2 *H,
+                            int64_t ldh, int32_t kc0, int32_t kcn, float *gW, int accumulate_gW, double *partial,
+                            const int32_t *idx, double *g_lm, int accumulate_lm, int fast, int nsm, cudaStream_t st);
+
 // ---- tcgen05 contraction (k_tc.cu) ----------------------------------------
 struct TcItem {
     int32_t slot, N;
