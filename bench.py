@@ -325,6 +325,24 @@ def measure_batched(psf, prec, steps=2, which="c4"):
                 adj[ap]["tc_kernel_frac_of_peak"] = adj[ap]["tc_kernel_tflops"] / peaks["bf16_tflops"]
         plan.set_opts(prec=prec)
         adj["speedup_tc_over_fp32"] = adj["fp32"]["ms"] / adj[prec]["ms"] if prec in adj and prec != "fp32" else None
+    per_size = None
+    if which == "c3":   # the exact method per cutout size (each size group alone)
+        per_size = {}
+        for N in sorted(set(int(x) for x in bg.npix)):
+            sel = np.nonzero(bg.npix == N)[0]
+            bN = psf.Batch(bg.lm[sel], N, bg.cell_rad)
+            oN = torch.empty(bN.total(), dtype=torch.float32, device="cuda")
+            plan.forward("exact", bN, out=oN)
+            torch.cuda.synchronize()
+            plan.profile_read()
+            plan.profile_enable(True)
+            plan.forward("exact", bN, out=oN)
+            torch.cuda.synchronize()
+            kms, nkc, _ = plan.profile_read()
+            plan.profile_enable(False)
+            tf = 4.0 * K * len(sel) * N * N / (kms * 1e-3) / 1e12
+            per_size[f"{N}px"] = {"positions": int(len(sel)), "kernel_ms": kms, "kernel_tflops": tf,
+                                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"]}
     st = plan.sync_status()
     plan.close()
     if st != 0:
@@ -332,8 +350,8 @@ def measure_batched(psf, prec, steps=2, which="c4"):
     name = "meerkat64_2h_8ch_bda_256pos_64px" if which == "c4" else "meerkat64_2h_8ch_bda_4096pos_32to256px"
     return {"workload": name, "nvis": K, "positions": bg.npos, "npix": sorted(set(int(x) for x in bg.npix)),
             "value": terms / (ms * 1e-3), "unit": "terms/s", "ms_per_step": ms, "methods": ["exact", "uv", "img"],
-            "kernel": "k_psf_kr (tcgen05 batched contraction)", "per_method": per, "peak_source": src,
-            "adjoint_exact": adj}
+            "kernel": "k_psf_kr (tcgen05 batched contraction, persistent, work queue)", "per_method": per,
+            "peak_source": src, "adjoint_exact": adj, "exact_per_cutout_size": per_size}
 
 
 # Executed warp-instructions per position of k_img_grid (ncu smsp__inst_executed.sum of one
@@ -783,6 +801,7 @@ def main():
     fwhm = None if args.no_fwhm or rank != 0 else measure_fwhm(psf, args.prec)
     facets = None if args.no_facets or rank != 0 else measure_facets(psf, plan)
     batched = None if args.no_batched else measure_batched(psf, args.prec)
+    batched_c3 = None if args.no_batched else measure_batched(psf, args.prec, steps=1, which="c3")
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
     if rank == 0:
@@ -812,7 +831,7 @@ def main():
                            "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
                            "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "precision_ladder": ladder,
-                "batched": batched, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
+                "batched": batched, "batched_c3": batched_c3, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
                 "parity": parity,
                 "gpu_launches": int(nk), "clocks": clocks}
         print(json.dumps(line), flush=True)

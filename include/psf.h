@@ -84,6 +84,15 @@ extern "C" {
 #define PSF_COMPLEX_OUT       8u
 
 /* ---- contraction algorithm (psf_opts_t.algo) ---------------------------- */
+/* PSF_ALGO_AUTO: positions of one cutout size (a multiple of 32 up to 256) take the
+ * batched form when their group is large enough, the rest the per-cutout form.  The
+ * batched form runs every such group of a call in one persistent launch per visibility
+ * chunk (one CTA per SM pulling items from a work queue).  An autotuner, run on the first
+ * batched call of a plan for each weight class (real / complex weights, FP16 / BF16) and
+ * for each cutout size first met, times probes over the first 2^19 visibilities (the
+ * call then synchronizes its stream): the items per SM of the persistent launch, and per
+ * cutout size the group size from which the batched form beats the per-cutout form.  The
+ * results are kept by the plan. */
 #define PSF_ALGO_AUTO 0   /* per-cutout form for small batches, batched otherwise */
 #define PSF_ALGO_CUTOUT 1 /* per-cutout separable form, split over visibilities  */
 

@@ -28,6 +28,8 @@
 
 #include <cuda.h>
 
+#include <algorithm>
+
 namespace psf {
 namespace {
 using namespace tc;
@@ -44,6 +46,9 @@ constexpr int kKrMmaWarp = 21;
 constexpr int kKrInWarp = 22;
 constexpr int kKrThreads = 23 * 32;
 constexpr int kKrFoldStages = 64;
+// roles that read each item index from the ring: 16 generator warps, 4 fold warps, the
+// MMA issuer and the uv ring (one arrival each)
+constexpr int kKrItemReaders = kKrGenWarps + 4 + 1 + 1;
 // Slot-reuse parity waits stay unambiguous only with at most as many generator groups
 // as operand stages (see k_tc.cu).
 static_assert(kKrGroups <= kKrStages && kKrGroups <= kKrIn, "generator groups exceed a ring depth");
@@ -52,6 +57,7 @@ constexpr uint32_t kKrBTile = 256 * 128;   // 256 pixels x 64 K' x 2 B
 constexpr uint32_t kKrInSlot = 2 * kKrKS * 8;  // uv per stage (64 visibilities in the real form)
 constexpr uint32_t kKrSmemBytes =
     kKrStages * (kKrATile + kKrBTile) + kKrIn * kKrInSlot + 512 + 1024;
+static_assert((2 * kKrStages + 2 * kKrIn + 3 + 5) * 8 + 2 * 4 + 8 <= 512, "barrier block exceeds its reserve");
 
 // One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (theta (n0 + r) + phi)),
 // r = 0..31, as eight interleaved 4-pixel pieces in packed FP32x2 recurrences.
@@ -143,8 +149,9 @@ __device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&o
 
 template <int BF16, int REAL>
 __global__ void __launch_bounds__(kKrThreads, 1)
-    k_psf_kr(const __grid_constant__ CUtensorMap wmap, const KrItem *__restrict__ items, const float2 *__restrict__ uv,
-             int32_t kchunk0, float cell, const int64_t *__restrict__ out_off, float *__restrict__ out, int *err) {
+    k_psf_kr(const __grid_constant__ CUtensorMap wmap, const KrItem *__restrict__ items, int nitems,
+             int *__restrict__ queue, const float2 *__restrict__ uv, int32_t kchunk0, float cell,
+             const int64_t *__restrict__ out_off, float *__restrict__ out, int *err) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t *a_base = smem;
@@ -157,15 +164,16 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     uint64_t *acc_full = in_empty + kKrIn;
     uint64_t *acc_empty = acc_full + 1;
     uint64_t *done_bar = acc_empty + 1;
-    uint32_t *s_tmem = (uint32_t *)(done_bar + 1);
+    uint64_t *item_full = done_bar + 1;    // [2]: the item index of ring slot written
+    uint64_t *item_empty = item_full + 2;  // [2]: every role has read it
+    uint64_t *item_done = item_empty + 2;  // the fold warps have finished an item
+    int *s_item = (int *)(item_done + 1);   // [2]
+    uint32_t *s_tmem = (uint32_t *)(s_item + 2);
     volatile int *s_abort = (volatile int *)(s_tmem + 1);
     volatile int no_abort = 0;   // teardown waits ignore the abort flag
 
-    const KrItem it = items[blockIdx.x];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int KS = REAL ? 2 * kKrKS : kKrKS;   // visibilities per stage (64 K' either way)
-    const int nst = (it.ke - it.kb + KS - 1) / KS;
-    const int nfold = (nst + kKrFoldStages - 1) / kKrFoldStages;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kKrStages; ++s) {
@@ -179,6 +187,11 @@ __global__ void __launch_bounds__(kKrThreads, 1)
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 4);
         mbar_init(done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&item_full[b], 1);
+            mbar_init(&item_empty[b], kKrItemReaders);
+        }
+        mbar_init(item_done, 4);
         *s_abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -191,93 +204,148 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *s_tmem;   // columns [0, 256): active accumulator, [256, 512): running sum
 
+    // Every role walks the same item sequence from the two-slot ring: the li-th item of
+    // this CTA is in slot li & 1; a role reads it, acknowledges (item_empty) and keeps the
+    // index in registers.  item < 0 ends the sequence.  Stages and fold ranges are
+    // numbered globally across the CTA's items, so the operand rings and the accumulator
+    // run on without draining between items.
+    auto next_item = [&](int li, bool ack) -> int {
+        const int slot = li & 1;
+        if (!wait_bounded(&item_full[slot], (uint32_t)(li >> 1) & 1u, s_abort, err)) return -2;
+        const int item = *(volatile int *)&s_item[slot];
+        if (ack) mbar_arrive(&item_empty[slot]);
+        return item;
+    };
+    auto item_stages = [&](const KrItem &it) { return (it.ke - it.kb + KS - 1) / KS; };
+
     if (warp < kKrGenWarps) {
         // ------------------------------------------------------------ pixel twiddles
-        const int half = it.N / 2;
         const int grp = warp / kKrGroupWarps, gw = warp % kKrGroupWarps;
         uint32_t off8[8];
         stmatrix_offsets(lane, off8);
-        for (int s_i = grp; s_i < nst; s_i += kKrGroups) {
-            const int slot = s_i % kKrStages;
-            const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
-            const int islot = s_i % kKrIn;
-            bool ok = wait_bounded(&in_full[islot], (uint32_t)(s_i / kKrIn) & 1u, s_abort, err);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            const float2 *in_uv = reinterpret_cast<const float2 *>(in_base + islot * kKrInSlot);
-            float2 uva, uvb;
-            if (REAL) {
-                uva = in_uv[2 * lane];
-                uvb = in_uv[2 * lane + 1];
-            } else {
-                uva = in_uv[lane];
-                uvb = uva;
+        int g0 = 0;   // global index of the current item's first stage
+        bool ok = true;
+        for (int li = 0; ok; ++li) {
+            int item = -2;
+            if (lane == 0) item = next_item(li, true);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item < 0) { ok = item == -1; break; }
+            const KrItem it = items[item];
+            const int nst = item_stages(it);
+            const int half = it.N / 2;
+            // this group's stages of the item: global g = g0 + s with g = grp (mod 4)
+            for (int s = ((grp - g0) % kKrGroups + kKrGroups) % kKrGroups; s < nst; s += kKrGroups) {
+                const int g = g0 + s;
+                const int slot = g % kKrStages;
+                const uint32_t ph = (uint32_t)(g / kKrStages) & 1u;
+                const int islot = g % kKrIn;
+                bool w = wait_bounded(&in_full[islot], (uint32_t)(g / kKrIn) & 1u, s_abort, err);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                const float2 *in_uv = reinterpret_cast<const float2 *>(in_base + islot * kKrInSlot);
+                float2 uva, uvb;
+                if (REAL) {
+                    uva = in_uv[2 * lane];
+                    uvb = in_uv[2 * lane + 1];
+                } else {
+                    uva = in_uv[lane];
+                    uvb = uva;
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&in_empty[islot]);   // the input slot may be refilled
+                if (g >= kKrStages) {
+                    w = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
+                    if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                }
+                for (int r0 = gw * 32; r0 < it.npx; r0 += kKrGroupWarps * 32) {   // 32-pixel runs of this warp
+                    const int q = it.q0 + r0;
+                    const int jrow = q / it.N, i0 = q - jrow * it.N;   // inside one cutout row
+                    const uint32_t dst = smem_u32(b_base + slot * kKrBTile + r0 * 128);
+                    if (REAL)
+                        gen_run32_real<BF16>(dst, off8, make_float2(uva.x * cell, uvb.x * cell), make_float2(0.f, 0.f),
+                                             i0 - half,
+                                             make_float2(uva.y * cell * (float)(jrow - half),
+                                                         uvb.y * cell * (float)(jrow - half)));
+                    else
+                        gen_run32<BF16>(dst, off8, uva.x * cell, i0 - half, uva.y * cell * (float)(jrow - half));
+                }
+                fence_proxy_async_smem();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&full[slot]);
             }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&in_empty[islot]);   // the input slot may be refilled
-            if (s_i >= kKrStages) {
-                ok = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
-                if (!__all_sync(0xffffffffu, ok)) break;
-            }
-            for (int r0 = gw * 32; r0 < it.npx; r0 += kKrGroupWarps * 32) {   // 32-pixel runs of this warp
-                const int q = it.q0 + r0;
-                const int jrow = q / it.N, i0 = q - jrow * it.N;   // inside one cutout row
-                const uint32_t dst = smem_u32(b_base + slot * kKrBTile + r0 * 128);
-                if (REAL)
-                    gen_run32_real<BF16>(dst, off8, make_float2(uva.x * cell, uvb.x * cell), make_float2(0.f, 0.f),
-                                         i0 - half,
-                                         make_float2(uva.y * cell * (float)(jrow - half),
-                                                     uvb.y * cell * (float)(jrow - half)));
-                else
-                    gen_run32<BF16>(dst, off8, uva.x * cell, i0 - half, uva.y * cell * (float)(jrow - half));
-            }
-            fence_proxy_async_smem();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&full[slot]);
+            g0 += nst;
         }
     } else if (warp == kKrTmaWarp) {
-        // ------------------------------------------------------------ weight tiles
+        // ------------------------------------------------------------ items and weight tiles
         if (lane == 0) {
-            const int x0 = (REAL ? 1 : 2) * (it.kb - kchunk0);   // K' column of the item's first visibility
-            for (int s_i = 0; s_i < nst; ++s_i) {
-                const int slot = s_i % kKrStages;
-                const uint32_t ph = (uint32_t)(s_i / kKrStages) & 1u;
-                if (s_i >= kKrStages && !wait_bounded(&empty[slot], ph ^ 1u, s_abort, err)) break;
-                mbar_arrive_expect_tx(&full[slot], kKrATile);
-                tma_load_2d(a_base + slot * kKrATile, &wmap, x0 + s_i * 2 * kKrKS, it.wrow, &full[slot]);
+            int g = 0;
+            for (int li = 0;; ++li) {
+                const int islot = li & 1;
+                if (li >= 2 && !wait_bounded(&item_empty[islot], (uint32_t)((li >> 1) - 1) & 1u, s_abort, err)) break;
+                // Items do not overlap in the pipeline: the next one is published once the
+                // fold warps have written the previous one out.  (With overlapping items the
+                // twiddle tile of one stage early in a CTA's later items came out wrong in
+                // about one item in ten on GB300; the cause was not found, see the design
+                // notes.)  The bubble costs a ring fill per item.
+                if (li >= 1 && !wait_bounded(item_done, (uint32_t)(li - 1) & 1u, s_abort, err)) break;
+                const int idx = atomicAdd(queue, 1);   // largest items first (host order)
+                const int item = idx < nitems ? idx : -1;
+                s_item[islot] = item;
+                mbar_arrive(&item_full[islot]);   // release: the index is visible to the waiters
+                if (item < 0) break;
+                const KrItem it = items[item];
+                const int nst = item_stages(it);
+                const int x0 = (REAL ? 1 : 2) * (it.kb - kchunk0);   // K' column of the item's first visibility
+                bool stop = false;
+                for (int s = 0; s < nst; ++s, ++g) {
+                    const int slot = g % kKrStages;
+                    const uint32_t ph = (uint32_t)(g / kKrStages) & 1u;
+                    if (g >= kKrStages && !wait_bounded(&empty[slot], ph ^ 1u, s_abort, err)) { stop = true; break; }
+                    mbar_arrive_expect_tx(&full[slot], kKrATile);
+                    tma_load_2d(a_base + slot * kKrATile, &wmap, x0 + s * 2 * kKrKS, it.wrow, &full[slot]);
+                }
+                if (stop) break;
             }
         }
         __syncwarp();
     } else if (warp == kKrMmaWarp) {
         // ------------------------------------------------------------ MMA issue
         if (lane == 0) {
-            const uint32_t idesc = idesc_f16(128, it.npx, BF16);
             // short per-stage issue path (the MMA issue blocks this thread): slot and
             // phase by increment, descriptors by adding the slot offset to the address
             // field, constant accumulate flags
             const uint64_t ad0 = desc_sw128(smem_u32(a_base)), bd0 = desc_sw128(smem_u32(b_base));
-            int slot = 0, in_acc = 0, folds = 0;
+            int slot = 0, folds = 0;
             uint32_t ph = 0;
-            for (int s_i = 0; s_i < nst; ++s_i) {
-                if (!wait_bounded(&full[slot], ph, s_abort, err)) break;
-                if (in_acc == 0 && folds > 0 && !wait_bounded(acc_empty, (uint32_t)(folds - 1) & 1u, s_abort, err))
-                    break;
-                tc_fence_after();
-                const uint64_t ad = ad0 + (uint64_t)(slot * (kKrATile >> 4));
-                const uint64_t bd = bd0 + (uint64_t)(slot * (kKrBTile >> 4));
-                if (in_acc == 0) umma_f16(tmem, ad, bd, idesc, 0u);
-                else umma_f16(tmem, ad, bd, idesc, 1u);
-                umma_f16(tmem, ad + 2, bd + 2, idesc, 1u);
-                umma_f16(tmem, ad + 4, bd + 4, idesc, 1u);
-                umma_f16(tmem, ad + 6, bd + 6, idesc, 1u);
-                umma_commit(&empty[slot]);
-                if (++in_acc == kKrFoldStages || s_i == nst - 1) {
-                    umma_commit(acc_full);
-                    ++folds;
-                    in_acc = 0;
-                }
-                if (++slot == kKrStages) {
-                    slot = 0;
-                    ph ^= 1u;
+            bool stop = false;
+            for (int li = 0; !stop; ++li) {
+                const int item = next_item(li, true);
+                if (item < 0) break;
+                const KrItem it = items[item];
+                const int nst = item_stages(it);
+                const uint32_t idesc = idesc_f16(128, it.npx, BF16);
+                int in_acc = 0;
+                for (int s = 0; s < nst; ++s) {
+                    if (!wait_bounded(&full[slot], ph, s_abort, err)) { stop = true; break; }
+                    if (in_acc == 0 && folds > 0 &&
+                        !wait_bounded(acc_empty, (uint32_t)(folds - 1) & 1u, s_abort, err)) { stop = true; break; }
+                    tc_fence_after();
+                    const uint64_t ad = ad0 + (uint64_t)(slot * (kKrATile >> 4));
+                    const uint64_t bd = bd0 + (uint64_t)(slot * (kKrBTile >> 4));
+                    if (in_acc == 0) umma_f16(tmem, ad, bd, idesc, 0u);
+                    else umma_f16(tmem, ad, bd, idesc, 1u);
+                    umma_f16(tmem, ad + 2, bd + 2, idesc, 1u);
+                    umma_f16(tmem, ad + 4, bd + 4, idesc, 1u);
+                    umma_f16(tmem, ad + 6, bd + 6, idesc, 1u);
+                    umma_commit(&empty[slot]);
+                    if (++in_acc == kKrFoldStages || s == nst - 1) {
+                        umma_commit(acc_full);
+                        ++folds;
+                        in_acc = 0;
+                    }
+                    if (++slot == kKrStages) {
+                        slot = 0;
+                        ph ^= 1u;
+                    }
                 }
             }
             umma_commit(done_bar);
@@ -287,53 +355,74 @@ __global__ void __launch_bounds__(kKrThreads, 1)
     } else if (warp == kKrInWarp) {
         // ------------------------------------------------------------ uv input ring
         if (lane == 0) {
-            int issued = 0;
-            for (int s_i = 0; s_i < nst; ++s_i) {
-                const int islot = s_i % kKrIn;
-                if (s_i >= kKrIn && !wait_bounded(&in_empty[islot], (uint32_t)(s_i / kKrIn - 1) & 1u, s_abort, err))
-                    break;
-                mbar_arrive_expect_tx(&in_full[islot], KS * 8);
-                bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s_i * KS, KS * 8, &in_full[islot]);
-                issued = s_i + 1;
+            int g = 0, issued = 0;
+            bool stop = false;
+            for (int li = 0; !stop; ++li) {
+                const int item = next_item(li, true);
+                if (item < 0) break;
+                const KrItem it = items[item];
+                const int nst = item_stages(it);
+                for (int s = 0; s < nst; ++s, ++g) {
+                    const int islot = g % kKrIn;
+                    if (g >= kKrIn && !wait_bounded(&in_empty[islot], (uint32_t)(g / kKrIn - 1) & 1u, s_abort, err)) {
+                        stop = true;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&in_full[islot], KS * 8);
+                    bulk_g2s(in_base + islot * kKrInSlot, uv + it.kb + s * KS, KS * 8, &in_full[islot]);
+                    issued = g + 1;
+                }
             }
             // every copy has landed before the CTA exits (the last use of each slot)
-            for (int s_i = max(0, issued - kKrIn); s_i < issued; ++s_i)
-                wait_bounded(&in_full[s_i % kKrIn], (uint32_t)(s_i / kKrIn) & 1u, &no_abort, err);
+            for (int q = max(0, issued - kKrIn); q < issued; ++q)
+                wait_bounded(&in_full[q % kKrIn], (uint32_t)(q / kKrIn) & 1u, &no_abort, err);
         }
         __syncwarp();
     } else {
         // ------------------------------------------------------------ fold / output
         const int qw = warp - kKrFoldWarp0;          // TMEM lane quarter
         const int row = qw * 32 + lane;              // position row of the tile
-        const bool row_ok = row < it.npos;
-        float *dst = out + (row_ok ? out_off[it.slot0 + row] : 0) + it.q0;
         const uint32_t ta = tmem + ((uint32_t)(qw * 32) << 16);
-        for (int f = 0; f < nfold; ++f) {
-            const bool ok = wait_bounded(acc_full, (uint32_t)f & 1u, s_abort, err);
-            if (!__all_sync(0xffffffffu, ok)) break;
-            tc_fence_after();
-            const bool last = (f == nfold - 1);
-            for (int c0 = 0; c0 < it.npx; c0 += 16) {
-                float v[16];
-                tmem_ld16(ta + (uint32_t)c0, v);
-                if (f > 0) {
-                    float sacc[16];
-                    tmem_ld16(ta + 256u + (uint32_t)c0, sacc);
+        int F = 0;   // global fold range index
+        bool ok = true;
+        for (int li = 0; ok; ++li) {
+            int item = -2;
+            if (lane == 0) item = next_item(li, true);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item < 0) break;
+            const KrItem it = items[item];
+            const int nfold = (item_stages(it) + kKrFoldStages - 1) / kKrFoldStages;
+            const bool row_ok = row < it.npos;
+            float *dst = out + (row_ok ? out_off[it.slot0 + row] : 0) + it.q0;
+            for (int f = 0; f < nfold; ++f, ++F) {
+                const bool w = wait_bounded(acc_full, (uint32_t)F & 1u, s_abort, err);
+                if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+                tc_fence_after();
+                const bool last = (f == nfold - 1);
+                for (int c0 = 0; c0 < it.npx; c0 += 16) {
+                    float v[16];
+                    tmem_ld16(ta + (uint32_t)c0, v);
+                    if (f > 0) {
+                        float sacc[16];
+                        tmem_ld16(ta + 256u + (uint32_t)c0, sacc);
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) v[e] += sacc[e];
-                }
-                if (last) {
-                    if (row_ok) {
-#pragma unroll
-                        for (int e = 0; e < 16; ++e) atomicAdd(dst + c0 + e, v[e]);
+                        for (int e = 0; e < 16; ++e) v[e] += sacc[e];
                     }
-                } else {
-                    tmem_st16(ta + 256u + (uint32_t)c0, v);
+                    if (last) {
+                        if (row_ok) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) atomicAdd(dst + c0 + e, v[e]);
+                        }
+                    } else {
+                        tmem_st16(ta + 256u + (uint32_t)c0, v);
+                    }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(acc_empty);
             }
-            tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(acc_empty);
+            if (ok && lane == 0) mbar_arrive(item_done);
         }
     }
     tc_fence_before();
@@ -345,25 +434,30 @@ __global__ void __launch_bounds__(kKrThreads, 1)
 }  // namespace
 
 template <int BF16, int REAL>
-static cudaError_t launch_kr_t(const CUtensorMap *m, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
-                               float cell, const int64_t *out_off, float *out, int *err, cudaStream_t st) {
+static cudaError_t launch_kr_t(const CUtensorMap *m, const KrItem *items, int nitems, int *queue, int nctas,
+                               const float2 *uv, int32_t kchunk0, float cell, const int64_t *out_off, float *out,
+                               int *err, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_psf_kr<BF16, REAL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kKrSmemBytes);
     if (e != cudaSuccess) return e;
-    k_psf_kr<BF16, REAL><<<nitems, kKrThreads, kKrSmemBytes, st>>>(*m, items, uv, kchunk0, cell, out_off, out, err);
+    k_psf_kr<BF16, REAL><<<nctas, kKrThreads, kKrSmemBytes, st>>>(*m, items, nitems, queue, uv, kchunk0, cell,
+                                                                   out_off, out, err);
     return cudaGetLastError();
 }
 
-cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
-                          float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
+cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, int *queue, int nctas, const float2 *uv,
+                          int32_t kchunk0, float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
                           cudaStream_t st) {
     if (nitems <= 0) return cudaSuccess;
+    nctas = std::max(1, std::min(nctas, nitems));
+    cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return e;
     const CUtensorMap *m = (const CUtensorMap *)wmap;
     if (bf16)
-        return real ? launch_kr_t<1, 1>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st)
-                    : launch_kr_t<1, 0>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st);
-    return real ? launch_kr_t<0, 1>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st)
-                : launch_kr_t<0, 0>(m, items, nitems, uv, kchunk0, cell, out_off, out, err, st);
+        return real ? launch_kr_t<1, 1>(m, items, nitems, queue, nctas, uv, kchunk0, cell, out_off, out, err, st)
+                    : launch_kr_t<1, 0>(m, items, nitems, queue, nctas, uv, kchunk0, cell, out_off, out, err, st);
+    return real ? launch_kr_t<0, 1>(m, items, nitems, queue, nctas, uv, kchunk0, cell, out_off, out, err, st)
+                : launch_kr_t<0, 0>(m, items, nitems, queue, nctas, uv, kchunk0, cell, out_off, out, err, st);
 }
 
 // 2-D tensor map over the FP16/BF16 weight buffer: dim0 = pitch elements (2 KC for

@@ -17,6 +17,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <thread>
@@ -121,6 +122,15 @@ struct psf_plan_s {
     std::vector<std::unique_ptr<Grid>> grids;
     DevBuf gpairs;   // per-call pair records of the gridded form
     DevBuf err;          // int: device-side wait timeouts
+    DevBuf queue;        // int: work queue of the persistent batched kernel
+    // autotuner of the batched form, per weight class (bit 0 real weights, bit 1 BF16):
+    // items per SM and, per cutout size, the smallest group the batched form takes
+    struct KrTune {
+        bool done = false;
+        int items_per_cta = 4;
+        std::map<int, int> min_group;
+    };
+    KrTune tune[4];
     // per-call workspace
     DevBuf meta;         // positions, sizes, offsets, tiles
     DevBuf wbuf;         // weights of a chunk of positions
@@ -561,92 +571,114 @@ constexpr size_t kWeightBudget = size_t(4) << 30;   // weights of one position c
 constexpr size_t kW16Budget = size_t(1) << 30;      // FP16 weights of one batched chunk (bytes)
 constexpr int kKrMinGroup = 32;                     // positions of one size for the batched form
 
-// Batched tensor-core path for one group of positions with the same cutout size N
-// (N a multiple of 32, <= 256): weights of the group for a chunk of visibilities are
-// written as FP16/BF16 pairs, then the Khatri-Rao kernel accumulates every
-// (128-position tile, 256-pixel tile, visibility range) item into the zeroed output.
-int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int> &idx, int N, float *out,
-           cudaStream_t st) {
-    const int np = (int)idx.size();
-    const int ntile = (np + 127) / 128;
-    const int rows = ntile * 128;
-    const int64_t K = p->nvis;
+// One size group of the batched form: positions idx (batch indices) of cutout size N.
+struct KrGroup {
+    int N;
+    std::vector<int> idx;
+};
+
+// Batched tensor-core path for groups of positions with cutout sizes N (multiples of 32,
+// <= 256).  Per chunk of visibilities the weights of every group are written as FP16/BF16
+// rows into one buffer (each group padded to whole 128-position tiles), then one
+// persistent launch of the Khatri-Rao kernel (one CTA per SM) pulls (128-position tile,
+// 256-pixel tile, visibility range) items from an atomic queue and accumulates them into
+// the zeroed output.  Every item is 128 positions x 256 pixels, so its cost is its
+// visibility range: the ranges are equal, items_per_cta x SMs of them at least (fewer
+// when a range would drop below one 64-stage accumulation run).  kmax < nvis restricts
+// the call to the first kmax visibilities (the autotuner's probes); ms_out (optional)
+// receives the summed time of the contraction launches (the stream is synchronized).
+int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<KrGroup> &groups, float *out,
+           cudaStream_t st, int items_per_cta, int64_t kmax = -1, double *ms_out = nullptr) {
+    const int64_t K = kmax > 0 ? std::min<int64_t>(kmax, p->nvis) : p->nvis;
     const int bf16 = prec_bf16(p->opts.prec);
     // Methods 1 and 2 have real weights (unless windowed): one K' column per visibility,
     // 64-visibility stages; complex weights: two columns, 32-visibility stages.
     const int real = method != kExact && p->d.win == 0;
     const int64_t ks = real ? 64 : 32;
     const size_t bytes_per = real ? 2 : 4;
+    // combined rows: group g occupies rows [row0_g, row0_g + 128 ntile_g)
+    std::vector<float4> pos;
+    std::vector<int32_t> slot_of_row, npix;
+    std::vector<int64_t> outo;
+    std::vector<int> row0(groups.size()), slot0(groups.size());
+    int rows = 0;
+    for (size_t g = 0; g < groups.size(); ++g) {
+        const int np = (int)groups[g].idx.size();
+        row0[g] = rows;
+        slot0[g] = (int)pos.size();
+        for (int i = 0; i < np; ++i) {
+            pos.push_back(h.pos[groups[g].idx[i]]);
+            outo.push_back(h.out_off[groups[g].idx[i]]);
+            npix.push_back(groups[g].N);
+        }
+        const int ntile = (np + 127) / 128;
+        for (int r = 0; r < ntile * 128; ++r) slot_of_row.push_back(r < np ? slot0[g] + r : -1);
+        rows += ntile * 128;
+    }
+    const int npos = (int)pos.size();
+    if (npos == 0) return PSF_OK;
     int64_t KC = (int64_t)(kW16Budget / ((size_t)rows * bytes_per)) / 64 * 64;
     KC = std::max<int64_t>(64, std::min<int64_t>(KC, (K + 63) / 64 * 64));
     const int64_t nchunk = (K + KC - 1) / KC;
-    const int ptiles = N * N / 256;
-    // positions, per-row slots, per-slot output offsets (uploaded once), items per chunk
-    std::vector<float4> pos(np);
-    std::vector<int32_t> slot_of_row(rows, -1), npix(np, N);
-    std::vector<int64_t> outo(np);
-    for (int i = 0; i < np; ++i) {
-        pos[i] = h.pos[idx[i]];
-        slot_of_row[i] = i;
-        outo[i] = h.out_off[idx[i]];
-    }
+    int64_t nbase = 0;   // (position tile, pixel tile) pairs
+    for (const auto &g : groups) nbase += (int64_t)((g.idx.size() + 127) / 128) * (g.N * g.N / 256);
     PSF_TRY(p->w16.reserve((size_t)rows * KC * bytes_per));
+    PSF_TRY(p->queue.reserve(sizeof(int)));
     CUtensorMapStub wmap;
     int s = make_weight_map(&wmap, p->w16.p, bf16, real ? KC : 2 * KC, rows);
     if (s) return s;
-    const int64_t nbase = (int64_t)ntile * ptiles;
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    double ms_total = 0.0;
+    if (ms_out) {
+        PSF_TRY(cudaEventCreate(&t0));
+        PSF_TRY(cudaEventCreate(&t1));
+    }
     for (int64_t c = 0; c < nchunk; ++c) {
         const int64_t kc0 = c * KC, kcn = std::min<int64_t>(KC, K - kc0);
         const int64_t nst = (kcn + ks - 1) / ks;
-        // visibility splits: the number of CTAs (tiles x splits, one CTA per SM) should
-        // fill whole waves; among split counts giving >= 2 waves (and >= 64 stages per
-        // split) take the one with the best last-wave occupancy
-        int64_t nsplit = 1;
-        {
-            const int64_t maxs = std::max<int64_t>(1, nst / 64);
-            double best = -1.0;
-            for (int64_t cand = 1; cand <= std::min<int64_t>(maxs, 256); ++cand) {
-                const int64_t ctas = nbase * cand;
-                const int64_t waves = (ctas + p->nsm - 1) / p->nsm;
-                const double eff = (double)ctas / (double)(waves * p->nsm);
-                const double score = eff - (waves < 2 && cand < maxs ? 0.5 : 0.0) - 0.002 * (double)cand;
-                if (score > best) { best = score; nsplit = cand; }
-            }
-        }
+        // equal visibility ranges: enough items for items_per_cta per CTA, ranges of at
+        // least one accumulation run (64 stages)
+        const int64_t target = (int64_t)std::max(1, items_per_cta) * p->nsm;
+        int64_t nsplit = std::max<int64_t>(1, std::min<int64_t>((target + nbase - 1) / nbase, nst / 64));
         const int64_t sper = (nst + nsplit - 1) / nsplit;
         nsplit = (nst + sper - 1) / sper;
         std::vector<KrItem> items;
         items.reserve(nbase * nsplit);
-        for (int t = 0; t < ntile; ++t)
-            for (int64_t sp = 0; sp < nsplit; ++sp)
-                for (int q = 0; q < ptiles; ++q) {
-                    KrItem it;
-                    it.wrow = t * 128;
-                    it.npos = std::min(128, np - t * 128);
-                    it.slot0 = t * 128;
-                    it.N = N;
-                    it.q0 = q * 256;
-                    it.npx = 256;
-                    it.kb = (int32_t)(kc0 + sp * sper * ks);
-                    it.ke = (int32_t)std::min<int64_t>(kc0 + kcn, kc0 + (sp + 1) * sper * ks);
-                    items.push_back(it);
-                }
+        // the full ranges first, the shorter last range after them (largest first)
+        for (int64_t sp = 0; sp < nsplit; ++sp)
+            for (size_t g = 0; g < groups.size(); ++g) {
+                const int np = (int)groups[g].idx.size(), N = groups[g].N;
+                for (int t = 0; t < (np + 127) / 128; ++t)
+                    for (int q = 0; q < N * N / 256; ++q) {
+                        KrItem it;
+                        it.wrow = row0[g] + t * 128;
+                        it.npos = std::min(128, np - t * 128);
+                        it.slot0 = slot0[g] + t * 128;
+                        it.N = N;
+                        it.q0 = q * 256;
+                        it.npx = 256;
+                        it.kb = (int32_t)(kc0 + sp * sper * ks);
+                        it.ke = (int32_t)std::min<int64_t>(kc0 + kcn, kc0 + (sp + 1) * sper * ks);
+                        items.push_back(it);
+                    }
+            }
         const size_t off_pos = 0;
-        const size_t off_slot = align_up(off_pos + np * sizeof(float4), 16);
+        const size_t off_slot = align_up(off_pos + npos * sizeof(float4), 16);
         const size_t off_outo = align_up(off_slot + rows * sizeof(int32_t), 16);
-        const size_t off_npix = align_up(off_outo + np * sizeof(int64_t), 16);
-        const size_t off_items = align_up(off_npix + np * sizeof(int32_t), 16);
+        const size_t off_npix = align_up(off_outo + npos * sizeof(int64_t), 16);
+        const size_t off_items = align_up(off_npix + npos * sizeof(int32_t), 16);
         const size_t bytes = align_up(off_items + items.size() * sizeof(KrItem), 16);
         std::vector<char> blob(bytes, 0);
-        std::memcpy(blob.data() + off_pos, pos.data(), np * sizeof(float4));
+        std::memcpy(blob.data() + off_pos, pos.data(), npos * sizeof(float4));
         std::memcpy(blob.data() + off_slot, slot_of_row.data(), rows * sizeof(int32_t));
-        std::memcpy(blob.data() + off_outo, outo.data(), np * sizeof(int64_t));
-        std::memcpy(blob.data() + off_npix, npix.data(), np * sizeof(int32_t));
+        std::memcpy(blob.data() + off_outo, outo.data(), npos * sizeof(int64_t));
+        std::memcpy(blob.data() + off_npix, npix.data(), npos * sizeof(int32_t));
         std::memcpy(blob.data() + off_items, items.data(), items.size() * sizeof(KrItem));
         if ((s = upload_meta(p, blob.data(), bytes, st))) return s;
         char *dm = (char *)p->meta.p;
         if (c == 0) {
-            PSF_TRY(launch_zero_cutouts(out, (const int64_t *)(dm + off_outo), (const int32_t *)(dm + off_npix), np, st));
+            PSF_TRY(launch_zero_cutouts(out, (const int64_t *)(dm + off_outo), (const int32_t *)(dm + off_npix), npos,
+                                        st));
             p->n_kernels++;
         }
         PSF_TRY(launch_weights16(p->d, method, p->opts.flags, (const float4 *)(dm + off_pos),
@@ -666,18 +698,110 @@ int run_kr(psf_plan_s *p, int method, const BatchHost &h, const std::vector<int>
             p->prof_used++;
             PSF_TRY(cudaEventRecord(ev1, st));
         }
-        PSF_TRY(launch_psf_kr(&wmap, (const KrItem *)(dm + off_items), (int)items.size(), p->d.uv, (int32_t)kc0,
-                              (float)h.cell, (const int64_t *)(dm + off_outo), out, bf16, real, (int *)p->err.p, st));
+        if (ms_out) PSF_TRY(cudaEventRecord(t0, st));
+        PSF_TRY(launch_psf_kr(&wmap, (const KrItem *)(dm + off_items), (int)items.size(), (int *)p->queue.p, p->nsm,
+                              p->d.uv, (int32_t)kc0, (float)h.cell, (const int64_t *)(dm + off_outo), out, bf16, real,
+                              (int *)p->err.p, st));
+        if (ms_out) {
+            PSF_TRY(cudaEventRecord(t1, st));
+            PSF_TRY(cudaEventSynchronize(t1));
+            float ms = 0.f;
+            PSF_TRY(cudaEventElapsedTime(&ms, t0, t1));
+            ms_total += ms;
+        }
         if (p->prof) PSF_TRY(cudaEventRecord(ev2, st));
         p->n_contract++;
-        p->n_kernels++;
+        p->n_kernels += 2;   // the queue reset and the contraction
+    }
+    if (ms_out) {
+        *ms_out = ms_total;
+        cudaEventDestroy(t0);
+        cudaEventDestroy(t1);
     }
     return PSF_OK;
 }
 
+// Autotuner of the batched form, run on the first batched call of a plan for each weight
+// class (real / complex weights, operand type) and cached in the plan.  (1) Items per CTA:
+// the batched call of this batch's groups over a probe of the first kProbeVis
+// visibilities, timed for each candidate (2, 4, 8, 16 items per SM), into scratch output;
+// the fastest is kept.  (2) Per cutout size N present, the crossover between the forms:
+// the per-cutout form's time for one position and the batched form's time for one
+// 128-position tile over the same probe; the batched form takes a group of n positions
+// when ceil(n / 128) t_tile < n t_cutout.
+constexpr int64_t kProbeVis = int64_t(1) << 19;
+
+int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st, int64_t kmax = -1);
+
+int kr_tune(psf_plan_s *p, int method, const BatchHost &hall, const std::vector<KrGroup> &cand, cudaStream_t st,
+            psf_plan_s::KrTune &t) {
+    PSF_TRY(cudaStreamSynchronize(st));
+    const int64_t probe = std::min<int64_t>(kProbeVis, p->nvis);
+    // scratch output: packed offsets of the candidate groups' cutouts
+    BatchHost hs = hall;
+    int64_t run = 0;
+    for (const auto &g : cand)
+        for (int i : g.idx) {
+            hs.out_off[i] = run;
+            run += (int64_t)g.N * g.N;
+        }
+    DevBuf scratch;
+    PSF_TRY(scratch.reserve((size_t)std::max<int64_t>(run, 1) * sizeof(float)));
+    const bool prof = p->prof;
+    p->prof = false;
+    double best = 1e300;
+    int s = PSF_OK;
+    std::vector<KrGroup> big;
+    for (const auto &g : cand)
+        if ((int)g.idx.size() >= kKrMinGroup) big.push_back(g);
+    if (!t.done && !big.empty()) {
+        for (int ipc : {2, 4, 8, 16}) {
+            double ms = 0.0;
+            if ((s = run_kr(p, method, hs, big, (float *)scratch.p, st, ipc, probe, &ms))) break;
+            if (ms < best) { best = ms; t.items_per_cta = ipc; }
+        }
+        t.done = s == PSF_OK;
+    }
+    // crossover per size: one position per-cutout against one 128-position tile batched
+    for (const auto &g : cand) {
+        if (s) break;
+        if (t.min_group.count(g.N) || (int)g.idx.size() < 8) continue;
+        std::vector<KrGroup> one(1);
+        one[0].N = g.N;
+        one[0].idx.assign(g.idx.begin(), g.idx.begin() + std::min<size_t>(g.idx.size(), 128));
+        double t_tile = 0.0;
+        if ((s = run_kr(p, method, hs, one, (float *)scratch.p, st, t.items_per_cta, probe, &t_tile))) break;
+        const double lm[2] = {0.0, 0.0};   // cost does not depend on the position
+        psf_batch_t b1{};
+        b1.npos = 1;
+        b1.lm = lm;
+        b1.npix0 = g.N;
+        b1.cell_rad = hall.cell;
+        const psf_opts_t saved = p->opts;
+        p->opts.algo = PSF_ALGO_CUTOUT;
+        cudaEvent_t a, z;
+        PSF_TRY(cudaEventCreate(&a));
+        PSF_TRY(cudaEventCreate(&z));
+        PSF_TRY(cudaEventRecord(a, st));
+        s = run_forward(p, method, &b1, (float *)scratch.p, st, probe);
+        PSF_TRY(cudaEventRecord(z, st));
+        PSF_TRY(cudaEventSynchronize(z));
+        float t_cut = 0.f;
+        PSF_TRY(cudaEventElapsedTime(&t_cut, a, z));
+        cudaEventDestroy(a);
+        cudaEventDestroy(z);
+        p->opts = saved;
+        const double thr = t_cut > 0.f ? t_tile / (double)t_cut : 1e9;
+        t.min_group[g.N] = (int)std::max(1.0, std::min(128.0, std::ceil(thr)));
+    }
+    p->prof = prof;
+    PSF_TRY(cudaStreamSynchronize(st));
+    return s;
+}
+
 int run_forward_cplx(psf_plan_s *p, int method, const BatchHost &h, float *out, cudaStream_t st);
 
-int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st) {
+int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cudaStream_t st, int64_t kmax) {
     if (!p || !out) return PSF_EINVAL;
     const bool tc = p->opts.prec != PSF_FP32;
     const bool split = prec_split(p->opts.prec);
@@ -686,23 +810,39 @@ int run_forward(psf_plan_s *p, int method, const psf_batch_t *b, float *out, cud
     int s = prepare_batch(p, b, hall, cplx ? 128 : (tc ? 256 : 4096), cplx ? 2 : 1);
     if (s || hall.npos == 0) return s;
     if (cplx) return (tc && !split) ? run_forward_cplx(p, method, hall, out, st) : PSF_EUNSUPPORTED;
-    const int64_t K = p->nvis;
-    // Batched tensor-core form for large groups of one eligible size; the rest goes
-    // through the per-cutout form below.
+    if (kmax > 0 && !tc) return PSF_EINVAL;   // visibility probes (the autotuner) are tensor-core only
+    const int64_t K = kmax > 0 ? std::min<int64_t>(kmax, p->nvis) : p->nvis;
+    // Batched tensor-core form for groups of one eligible size that are large enough (the
+    // autotuner's crossover, else kKrMinGroup positions); the rest goes through the
+    // per-cutout form below.
     BatchHost h;
     h.cell = hall.cell;
-    if (tc && !split && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC)) {
-        std::vector<std::vector<int>> groups(257);
-        for (int i = 0; i < hall.npos; ++i) {
-            const int N = hall.npix[i];
-            if (N % 32 == 0 && N >= 32 && N <= 256) groups[N].push_back(i);
+    if (tc && !split && p->opts.algo == PSF_ALGO_AUTO && !(p->opts.flags & PSF_DETERMINISTIC) && kmax < 0) {
+        std::vector<KrGroup> present;
+        {
+            std::vector<std::vector<int>> by(257);
+            for (int i = 0; i < hall.npos; ++i) {
+                const int N = hall.npix[i];
+                if (N % 32 == 0 && N >= 32 && N <= 256) by[N].push_back(i);
+            }
+            for (int N = 32; N <= 256; N += 32)
+                if (!by[N].empty()) present.push_back(KrGroup{N, by[N]});
         }
+        const int real = method != kExact && p->d.win == 0;
+        psf_plan_s::KrTune &t = p->tune[(real ? 1 : 0) | (prec_bf16(p->opts.prec) ? 2 : 0)];
+        bool need = false;
+        for (const auto &g : present) need = need || (!t.min_group.count(g.N) && (int)g.idx.size() >= 8);
+        if (need && (s = kr_tune(p, method, hall, present, st, t))) return s;
+        std::vector<KrGroup> batched;
         std::vector<char> done(hall.npos, 0);
-        for (int N = 32; N <= 256; N += 32) {
-            if ((int)groups[N].size() < kKrMinGroup) continue;
-            if ((s = run_kr(p, method, hall, groups[N], N, out, st))) return s;
-            for (int i : groups[N]) done[i] = 1;
+        for (const auto &g : present) {
+            const auto f = t.min_group.find(g.N);
+            const int thr = f != t.min_group.end() ? f->second : kKrMinGroup;
+            if ((int)g.idx.size() < thr) continue;
+            batched.push_back(g);
+            for (int i : g.idx) done[i] = 1;
         }
+        if (!batched.empty() && (s = run_kr(p, method, hall, batched, out, st, t.items_per_cta))) return s;
         for (int i = 0; i < hall.npos; ++i)
             if (!done[i]) {
                 h.pos.push_back(hall.pos[i]);

@@ -142,8 +142,10 @@ struct KrItem {
     int32_t kb, ke;   // visibility range, kb - chunk start a multiple of the stage size (32 or 64)
 };
 // real != 0: real weights (Methods 1, 2), one K' column per visibility.
-cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, const float2 *uv, int32_t kchunk0,
-                          float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
+// Persistent: nctas CTAs (one per SM) pull items from the work queue (a device int,
+// zeroed by the launch) in array order (largest first).
+cudaError_t launch_psf_kr(const void *wmap, const KrItem *items, int nitems, int *queue, int nctas, const float2 *uv,
+                          int32_t kchunk0, float cell, const int64_t *out_off, float *out, int bf16, int real, int *err,
                           cudaStream_t st);
 int make_weight_map(void *map_out, void *w16, int bf16, int64_t pitch_elems, int64_t rows);
 int kr_smem_bytes();

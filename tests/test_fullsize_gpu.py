@@ -2,9 +2,9 @@
 the FP64 oracle on sampled pixels (the oracle evaluates each selected pixel over every
 visibility).
 
-* the batched (Khatri-Rao) kernel on groups of 128^2 and of 256^2 cutouts (32 positions
-  each, the smallest group the batched form takes) on the baseline-dependent-averaging
-  observation of the batched-positions workload (13.7 M visibilities);
+* the batched (Khatri-Rao) kernel on groups of 32^2, 64^2, 128^2 and 256^2 cutouts (32
+  positions each) on the baseline-dependent-averaging observation of the batched-positions
+  workload (13.7 M visibilities), and all four sizes in one persistent launch;
 * one 256 x 256 cutout through the per-cutout tensor-core kernel (two 128-row tiles of 256
   columns each);
 * the benchmark's fused call (Methods 1 and 2 in one pass, psf_approx_uv_img) on the
@@ -39,7 +39,7 @@ def _pixels(N, nrand, seed):
     return np.array(sorted(pix), np.int64)
 
 
-@pytest.mark.parametrize("N", [128, 256])
+@pytest.mark.parametrize("N", [32, 64, 128, 256])
 def test_batched_group_c3_observation(psf, N):
     """32 positions of one size within 1 degree: one 128-position tile of the batched
     kernel with N^2 / 256 pixel tiles each.  Eight of the positions are checked."""
@@ -103,3 +103,33 @@ def test_config2_fused_uv_img_row_and_column(psf):
         ref = oracle.psf(obs, mid, batch, pix_sel=pix)
         e = np.max(np.abs(got[pix] - ref[pix])) / np.max(np.abs(ref[pix]))
         assert e <= 1e-4, (mid, e)
+
+
+def test_batched_all_sizes_one_launch(psf):
+    """The batched-positions workload's mix: 40 positions of each size 32..256 in one call
+    (one persistent launch per visibility chunk pulls the items of every size group);
+    three positions per size checked on sampled pixels, all three methods."""
+    obs = obsgen.config3_obs()
+    rng = np.random.default_rng(obsgen.SEED_BASE + 77)
+    s = np.sin(np.radians(1.0))
+    npix = np.repeat(np.array([32, 64, 128, 256], np.int32), 40)
+    rng.shuffle(npix)
+    lm = rng.uniform(-s, s, size=(npix.size, 2))
+    cell = 1.5 * obsgen.ARCSEC
+    batch = obsgen.Batch(lm, npix, cell)
+    check = np.concatenate([np.nonzero(npix == N)[0][:3] for N in (32, 64, 128, 256)])
+    sub = obsgen.Batch(lm[check], npix[check], cell)
+    offs = obsgen.concat_pixels(batch)
+    soffs = obsgen.concat_pixels(sub)
+    pix = {int(p): _pixels(int(npix[p]), 5, int(p)) for p in check}
+    sub_sel = np.concatenate([soffs[q] + pix[int(p)] for q, p in enumerate(check)])
+    with psf.Plan(obs, prec="tc_fp16") as plan:
+        b = psf.Batch.from_obsgen(batch)
+        for name, mid in METHODS:
+            got = plan.forward(name, b).cpu().numpy().astype(np.float64)
+            ref = oracle.psf(obs, mid, sub, pix_sel=sub_sel)
+            for q, p in enumerate(check):
+                g, r = got[offs[p] + pix[int(p)]], ref[soffs[q] + pix[int(p)]]
+                e = np.max(np.abs(g - r)) / np.max(np.abs(r))
+                assert e <= 1e-4, (name, int(npix[p]), int(p), e)
+        assert plan.sync_status() == 0
