@@ -378,6 +378,15 @@ int psf_selftest_umma(const void *a_dev, const void *b_dev, float *d_dev, int n)
  * device context stays usable.  Synchronous. */
 int psf_selftest_timeout(int limit_ms);
 
+/* Diagnostic: the FP32 FMA throughput of the current device, the denominator of the
+ * FP32 path's roofline.  A grid of 8 CTAs of 256 threads per SM runs 16 independent
+ * FMA chains per thread, as scalar FMAs (packed = 0) or as packed FP32 pairs
+ * (packed = 1, fma.rn.f32x2); *flops_per_s receives the best of three timed launches
+ * after one warm-up (2 flops per FMA).  Allocates a small device buffer and a stream
+ * of its own.  PSF_EINVAL for a NULL pointer or packed not 0/1, PSF_ENOMEM,
+ * PSF_ECUDA.  Synchronous. */
+int psf_selftest_fma_rate(int packed, double *flops_per_s);
+
 #ifdef __cplusplus
 }
 #endif

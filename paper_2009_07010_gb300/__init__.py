@@ -6,5 +6,5 @@ include/psf.h.
 from ._lib import (EXACT, IMG, PSF_ALGO_AUTO, PSF_ALGO_CUTOUT, PSF_COMPLEX_OUT, PSF_DETERMINISTIC,  # noqa: F401
                    PSF_EINVAL, PSF_EUNSUPPORTED, PSF_IMG_LITERAL_THETA, PSF_OK, PSF_WTERM, UV,
                    PsfError, lib)
-from .api import Batch, Plan, SmearedPSF, selftest_umma, smeared_psf  # noqa: F401
+from .api import Batch, Plan, SmearedPSF, fma_rate, selftest_umma, smeared_psf  # noqa: F401
 from .build import build as build_library  # noqa: F401

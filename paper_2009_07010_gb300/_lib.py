@@ -21,7 +21,8 @@ EXACT, UV, IMG, IMG_GRID = 0, 1, 2, 3
 # every function include/psf.h declares
 EXPORTS = ["psf_plan", "psf_plan_set_opts", "psf_plan_set_windows", "psf_plan_set_weights", "psf_plan_nvis", "psf_exact", "psf_approx_uv", "psf_approx_img",
            "psf_approx_uv_img", "psf_approx_img_grid", "psf_img_grid_table", "psf_clean", "psf_fwhm", "psf_adjoint", "psf_sync_status", "psf_profile_enable", "psf_profile_read", "psf_plan_destroy",
-           "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc"]
+           "psf_strerror", "psf_selftest_umma", "psf_selftest_timeout", "psf_exact_noalloc",
+           "psf_selftest_fma_rate"]
 
 
 class CleanT(ctypes.Structure):
@@ -110,6 +111,8 @@ def lib(auto_build: bool = False):
             L.psf_strerror.restype = ctypes.c_char_p
             L.psf_selftest_timeout.argtypes = [I]
             L.psf_selftest_timeout.restype = I
+            L.psf_selftest_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double)]
+            L.psf_selftest_fma_rate.restype = I
             L.psf_selftest_umma.argtypes = [P, P, P, I]
             L.psf_selftest_umma.restype = I
             _LIB = L

@@ -258,6 +258,14 @@ def selftest_umma(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
     return d
 
 
+def fma_rate(packed: bool = False) -> float:
+    """Measured FP32 FMA throughput of the current device in flop/s (scalar FMAs, or
+    packed FP32 pairs with packed=True)."""
+    r = ctypes.c_double(0.0)
+    check(_lib.lib().psf_selftest_fma_rate(1 if packed else 0, ctypes.byref(r)), "psf_selftest_fma_rate")
+    return r.value
+
+
 class SmearedPSF(torch.autograd.Function):
     """Cutouts as a differentiable function of the positions (l0, m0) and, optionally,
     of the visibility weights W_k.

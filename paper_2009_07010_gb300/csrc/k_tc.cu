@@ -26,7 +26,10 @@
 //               TMEM accumulator while these warps read the first ones (tcgen05.ld),
 //               add them and add the sum into the CTA's FP32 partial tile in global
 //               memory.  Short TMEM accumulation runs bound the tensor-core rounding
-//               growth.
+//               growth.  Each add into the running sum is an error-free TwoSum: its
+//               rounding error goes back into the drained accumulator, on which the
+//               issuer's next range in that buffer accumulates (compensated summation
+//               with the correction carried by the tensor core).
 // Stages are handed over with mbarriers (input copies -> generators: `in_full`,
 // generators -> input warp: `in_empty`, generators -> MMA: `full`, MMA commit ->
 // generators: `empty`, MMA commit -> drain: `acc_full`, drain -> MMA: `acc_empty`).
@@ -64,8 +67,22 @@ constexpr int kDrainStages = 64;   // stages accumulated in TMEM between drains
 // Split precision: the tensor core's FP32 accumulation loses about 2^-24.5 of the running
 // value per added MMA (measured: the error of a cutout grows with the MMAs accumulated
 // between drains, 64-stage runs of 12 MMAs left ~1e-5), so the runs are 8 stages and the
-// drain warps keep the running sum in TMEM (FP32 adds, round to nearest).
+// drain warps keep the running sum in TMEM.
+//
+// Running sums of nearly equal terms (a coherent pixel such as the PSF peak, where every
+// range adds about the same value) do not round at random: the sum sits on its own ulp
+// grid and each add rounds the same way, so plain FP32 adds drift by up to ulp/2 per
+// range (about 1.5e-5 of the peak over 1500 ranges).  Every add is therefore a TwoSum,
+// s + v = t + e exactly, and e is written into the drained accumulator; the issuer's first
+// MMA of the next range in that buffer keeps it (accumulate) instead of clearing it.
 constexpr int kDrainStagesSplit = 8;
+
+// t = fl(a + b) and the exact rounding error e (a + b = t + e), any magnitudes (Knuth).
+__device__ __forceinline__ void two_sum(float a, float b, float &t, float &e) {
+    t = a + b;
+    const float bp = t - a;
+    e = (a - (t - bp)) + (b - bp);
+}
 constexpr int kATileBytes = 128 * 128;
 // One 32-row twiddle chain of one visibility (this lane), rows r = 0..31 of `base`:
 // value(r) = [w] exp(2 pi i theta (n0 + r)), written as an FP16/BF16 (re, im) pair at
@@ -473,7 +490,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint64_t bd = bd0 + (uint64_t)(slot * (b_stage >> 4));
                 const uint32_t dt = tmem + (uint32_t)(2 * q + b) * acc_cols;
                 // K' = 16 per MMA = 32 bytes (descriptor units of 16 B: +2) of the 128-byte row
-                if (r == q) umma_f16(dt, ad, bd, idesc, 0u);
+                // a range's first MMA clears the buffer, except issuer 0's from range 2 on:
+                // the drain has left the compensation of the running sum there
+                if (r == q) umma_f16(dt, ad, bd, idesc, (q == 0 && d >= 2) ? 1u : 0u);
                 else umma_f16(dt, ad, bd, idesc, 1u);
                 umma_f16(dt, ad + 2, bd + 2, idesc, 1u);
                 umma_f16(dt, ad + 4, bd + 4, idesc, 1u);
@@ -578,13 +597,14 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] += v2[e];
                 }
+                float cv[16];   // compensation for the buffer's next range
                 if (SPLIT) {
-                    if (d > 0) {
-                        float sv[16];
-                        tmem_ld16(tsum + (uint32_t)c0, sv);
+                    float sv[16];
 #pragma unroll
-                        for (int e = 0; e < 16; ++e) v[e] += sv[e];
-                    }
+                    for (int e = 0; e < 16; ++e) sv[e] = 0.f;
+                    if (d > 0) tmem_ld16(tsum + (uint32_t)c0, sv);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) two_sum(sv[e], v[e], v[e], cv[e]);
                     if (d < ndrain - 1) {
                         tmem_st16(tsum + (uint32_t)c0, v);
                     } else if (row_ok) {   // last range: the CTA's sum goes out once
@@ -592,21 +612,28 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int e = 0; e < 16; ++e)
                             if (cb + e < ncol_valid) dd[(cb + e) * cstride] = v[e];
                     }
-                    continue;
-                }
-                if (row_ok) {
-                    // eight loads in flight before their stores (one L2 round trip per eight)
+                } else {
 #pragma unroll
-                    for (int h = 0; h < 16; h += 8) {
-                        float o[8];
+                    for (int e = 0; e < 16; ++e) cv[e] = 0.f;
+                    if (row_ok) {
+                        // eight loads in flight before their stores (one L2 round trip per eight)
 #pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            o[e] = (d > 0 && cb + h + e < ncol_valid) ? dd[(cb + h + e) * cstride] : 0.f;
+                        for (int h = 0; h < 16; h += 8) {
+                            float o[8];
 #pragma unroll
-                        for (int e = 0; e < 8; ++e)
-                            if (cb + h + e < ncol_valid) dd[(cb + h + e) * cstride] = o[e] + v[h + e];
+                            for (int e = 0; e < 8; ++e)
+                                o[e] = (d > 0 && cb + h + e < ncol_valid) ? dd[(cb + h + e) * cstride] : 0.f;
+#pragma unroll
+                            for (int e = 0; e < 8; ++e) {
+                                float t;
+                                two_sum(o[e], v[h + e], t, cv[h + e]);
+                                if (cb + h + e < ncol_valid) dd[(cb + h + e) * cstride] = t;
+                            }
+                        }
                     }
                 }
+                // issuer 0's buffer b is accumulated on again by range d + 2
+                if (d + 2 < ndrain) tmem_st16(ta + (uint32_t)c0, cv);
             }
             tc_fence_before();
             __syncwarp();

@@ -117,6 +117,31 @@ cudaError_t launch_weights(const DevObs &o, int method, uint32_t flags, const fl
 // for every row; each warp writes 32 consecutive columns of one row at a time.
 constexpr int kRowsPerBlock = 32;
 
+// Rounding of the weights to 16 bits.  Round-to-nearest is biased on these data: with
+// natural weights most values W_k D_k sit just below the power of two W_k (small
+// decorrelation), where every one rounds up, and a PSF peak sums them coherently (a bias
+// of ~1e-5 of the peak over 2e8 visibilities).  Stochastic rounding (cvt.rs) is unbiased:
+// the random bits, a hash of (position, visibility), make the rounding errors average out
+// like independent ones.  The hash is deterministic, so a call is reproducible.
+__device__ __forceinline__ uint32_t sr_bits(uint32_t slot, uint32_t k) {
+    uint32_t h = k * 0x9E3779B1u ^ (slot + 0x7F4A7C15u) * 0x85EBCA77u;
+    h ^= h >> 16;
+    h *= 0x7FEB352Du;
+    h ^= h >> 15;
+    h *= 0x846CA68Bu;
+    h ^= h >> 16;
+    return h;
+}
+
+// (x, y) -> packed 16-bit pair, x in the low half (the layout of __floats2half2_rn)
+template <int BF16>
+__device__ __forceinline__ uint32_t pack_sr(float x, float y, uint32_t rbits) {
+    uint32_t d;
+    if (BF16) asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(y), "f"(x), "r"(rbits));
+    else asm("cvt.rs.f16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(y), "f"(x), "r"(rbits));
+    return d;
+}
+
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_t flags,
                                                    const float4 *__restrict__ pos,
@@ -138,15 +163,7 @@ __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_
             const float2 D = decorr<false, true>(o, method, flags, bin, r, pos[slot], z, z, nullptr);
             w = make_float2(Wk * D.x, Wk * D.y);
         }
-        uint32_t packed;
-        if (BF16) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(w.x, -w.y);
-            packed = *reinterpret_cast<uint32_t *>(&h);
-        } else {
-            __half2 h = __floats2half2_rn(w.x, -w.y);
-            packed = *reinterpret_cast<uint32_t *>(&h);
-        }
-        w16[(int64_t)row * kpitch + kk] = packed;
+        w16[(int64_t)row * kpitch + kk] = pack_sr<BF16>(w.x, -w.y, sr_bits((uint32_t)slot, (uint32_t)k));
     }
 }
 
@@ -182,15 +199,7 @@ __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, ui
             for (int e = 0; e < 2; ++e)
                 if (Wk[e] != 0.f) wv[e] = Wk[e] * decorr<false, true>(o, method, flags, bin[e], rr[e], P, z, z, nullptr).x;
         }
-        uint32_t packed;
-        if (BF16) {
-            __nv_bfloat162 h = __floats2bfloat162_rn(wv[0], wv[1]);
-            packed = *reinterpret_cast<uint32_t *>(&h);
-        } else {
-            __half2 h = __floats2half2_rn(wv[0], wv[1]);
-            packed = *reinterpret_cast<uint32_t *>(&h);
-        }
-        w16[(int64_t)row * kpitch2 + kp] = packed;
+        w16[(int64_t)row * kpitch2 + kp] = pack_sr<BF16>(wv[0], wv[1], sr_bits((uint32_t)slot, (uint32_t)(kc0 + 2 * kp)));
     }
 }
 
@@ -251,13 +260,7 @@ __global__ void __launch_bounds__(256) k_weights16_exact8(DevObs o, uint32_t fla
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             const float wr = Wk[j] * re[j] * inv, wi = Wk[j] * im[j] * inv;
-            if (BF16) {
-                __nv_bfloat162 h = __floats2bfloat162_rn(wr, -wi);
-                packed[j] = *reinterpret_cast<uint32_t *>(&h);
-            } else {
-                __half2 h = __floats2half2_rn(wr, -wi);
-                packed[j] = *reinterpret_cast<uint32_t *>(&h);
-            }
+            packed[j] = pack_sr<BF16>(wr, -wi, sr_bits((uint32_t)slot, (uint32_t)(k0 + j)));
         }
         uint4 *dst = reinterpret_cast<uint4 *>(w16 + (int64_t)row * kpitch + kk0);
         dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
@@ -348,6 +351,88 @@ cudaError_t launch_psf_fp32(const DevObs &o, const float2 *w, int64_t ldw, const
     k_psf_fp32<<<grid, 256, 0, st>>>(o.uv, o.uv_lo, w, ldw, o.nvis, tiles, kper, fp32t::cell_pair(cell), partial,
                                      split_stride);
     return cudaGetLastError();
+}
+
+// --------------------------------------------------------------- FP32 FMA rate
+// Denominator of the FP32 path's roofline: every thread runs kFmaChains independent
+// chains x <- x c + b (|c| < 1, so the values stay bounded), as scalar FMAs or as packed
+// pairs (fma.rn.f32x2, one instruction for two FMAs).  The last values are written so
+// that nothing is optimised away.
+constexpr int kFmaChains = 16;
+
+template <int PACKED>
+__global__ void __launch_bounds__(256) k_fma_rate(int iters, float seed, float *__restrict__ out) {
+    const float b = seed * 1e-3f + 1e-9f * threadIdx.x, c = 0.999f - 1e-7f * blockIdx.x;
+    float r = 0.f;
+    if (PACKED) {
+        unsigned long long x[kFmaChains], bb, cc;
+        asm("mov.b64 %0, {%1, %1};" : "=l"(bb) : "f"(b));
+        asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) {
+            const float v = seed + j;
+            asm("mov.b64 %0, {%1, %2};" : "=l"(x[j]) : "f"(v), "f"(-v));
+        }
+#pragma unroll 4
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int j = 0; j < kFmaChains; ++j) asm volatile("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(x[j]) : "l"(cc), "l"(bb));
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) {
+            float lo, hi;
+            asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x[j]));
+            r += lo + hi;
+        }
+    } else {
+        float x[kFmaChains];
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) x[j] = seed + j;
+#pragma unroll 8
+        for (int it = 0; it < iters; ++it)
+#pragma unroll
+            for (int j = 0; j < kFmaChains; ++j) x[j] = fmaf(x[j], c, b);
+#pragma unroll
+        for (int j = 0; j < kFmaChains; ++j) r += x[j];
+    }
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
+int selftest_fma_rate(int packed, double *flops_per_s) {
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return PSF_ECUDA;
+    const int blocks = nsm * 8, threads = 256, iters = 1 << 15;
+    float *out = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = PSF_OK;
+    double best = 0.0;
+    if (cudaMalloc(&out, sizeof(float) * blocks * threads) != cudaSuccess) return PSF_ENOMEM;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess) {
+        rc = PSF_ECUDA;
+    } else {
+        for (int rep = 0; rep < 4 && rc == PSF_OK; ++rep) {   // the first launch is warm-up
+            cudaEventRecord(e0, st);
+            if (packed) k_fma_rate<1><<<blocks, threads, 0, st>>>(iters, 1.0f + rep, out);
+            else k_fma_rate<0><<<blocks, threads, 0, st>>>(iters, 1.0f + rep, out);
+            cudaEventRecord(e1, st);
+            float ms = 0.f;
+            if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = PSF_ECUDA;
+                break;
+            }
+            const double flops = 2.0 * (packed ? 2 : 1) * kFmaChains * (double)iters * blocks * threads;
+            if (rep > 0 && ms > 0.f) best = std::max(best, flops / (ms * 1e-3));
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(out);
+    if (rc == PSF_OK) *flops_per_s = best;
+    return rc;
 }
 
 // --------------------------------------------------------------- split reduction

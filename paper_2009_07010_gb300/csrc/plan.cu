@@ -1683,6 +1683,11 @@ int psf_selftest_timeout(int limit_ms) {
     return selftest_timeout(limit_ms);
 }
 
+int psf_selftest_fma_rate(int packed, double *flops_per_s) {
+    if (!flops_per_s || (packed != 0 && packed != 1)) return PSF_EINVAL;
+    return selftest_fma_rate(packed, flops_per_s);
+}
+
 int psf_selftest_umma(const void *a, const void *b, float *d, int n) {
     if (!a || !b || !d || n < 16 || n > 256 || (n % 16)) return PSF_EINVAL;
     return selftest_umma(a, b, d, n);

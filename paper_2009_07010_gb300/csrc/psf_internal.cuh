@@ -130,6 +130,7 @@ cudaError_t launch_psf_tc_cplx(const DevObs &o, const float2 *w, int64_t ldw, co
                                int64_t part2, int *err, cudaStream_t st);
 int selftest_umma(const void *a, const void *b, float *d, int n);
 int selftest_timeout(int limit_ms);
+int selftest_fma_rate(int packed, double *flops_per_s);   // k_weights.cu
 
 // ---- batched tcgen05 contraction (k_kr.cu) ---------------------------------
 struct KrItem {

@@ -58,6 +58,17 @@ def test_umma_selftest_matches_matmul(psf, n):
     torch.testing.assert_close(d, ref, rtol=1e-5, atol=1e-4)
 
 
+def test_fma_rate_probe_is_physical(psf):
+    """The FP32 roofline's denominator: positive and below the lane count x 2 flops x a
+    2.5 GHz clock (x2 for packed pairs, which may issue two FMAs per lane)."""
+    import torch
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    bound = nsm * 128 * 2 * 2.5e9
+    s, p = psf.fma_rate(False), psf.fma_rate(True)
+    assert 0.25 * bound < s < bound, s
+    assert 0.25 * bound < p < 2 * bound, p
+
+
 # ------------------------------------------------------------------ workload 1 (full)
 @pytest.fixture(scope="module")
 def c1():
