@@ -133,12 +133,20 @@ def terms_per_step(K, batch, nmethods=3):
     return nmethods * K * batch.total_pixels()
 
 
+def step_config(args, K, N):
+    """The benchmark step's workload, the same object on both arms."""
+    return {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": N,
+            "positions_per_gpu": 1, "methods": ["exact", "uv", "img"], "precision": args.prec,
+            "accumulate": "f32", "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)",
+            "seed_array": obsgen.ARRAY_SEED}
+
+
 def run_reference(args, rank, world):
     """The FP64 CPU oracle as it stands, on bounded samples of the same workload."""
     if rank != 0:
         return 0
     import oracle
-    obs = obsgen.config2_obs()
+    obs = obsgen.config2_obs() if args.workload == "c2" else obsgen.config2_obs(hours=1.0)
     batch = obsgen.config2_batch()
     K = obs.nvis()
     N = int(batch.npix[0])
@@ -162,7 +170,7 @@ def run_reference(args, rank, world):
             "impl": "reference", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nvis": K, "npix": N, "sample_pixels_per_method": npx},
+            "config": step_config(args, K, N),
             "cpu_baseline": {"value": val, "unit": "terms/s", "cores": cores, "kind": "oracle",
                              "sample": f"{npx} random pixels per method of the 128x128 cutout, all {K} visibilities"},
             "e2e": {"value": val, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -877,10 +885,9 @@ def main():
         line = {"metric": "smeared-PSF px.vis terms/sec (exact + uv + img)", "value": value, "unit": "terms/s",
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": {"tc_fp16": "f16", "tc_bf16": "bf16", "fp32": "f32"}[args.prec], "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.workload == "c2" else WORKLOAD + "_1h", "nvis": K, "npix": int(batch_g.npix[0]), "positions_per_gpu": 1,
-                           "methods": ["exact", "uv", "img"], "precision": args.prec, "accumulate": "f32",
-                           "l2": "inputs exceed L2 (per-visibility tables 0.9 GB)", "seed_array": obsgen.ARRAY_SEED},
+                "dtype": {"tc_fp16": "f16", "tc_bf16": "bf16", "fp32": "f32", "tc_fp16x3": "f16x3",
+                          "tc_bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
+                "config": step_config(args, K, int(batch_g.npix[0])),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp32_plain": fp32, "precision_ladder": ladder,
                 "batched": batched, "batched_c3": batched_c3, "c5": c5, "img_grid": img_grid, "clean": clean, "fwhm": fwhm, "facets": facets,
                 "parity": parity,
