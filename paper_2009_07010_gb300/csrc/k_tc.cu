@@ -327,7 +327,14 @@ __global__ void __launch_bounds__(kThreads, 1)
     constexpr int kBMul = (MIR == 4 || MIR == 5) ? 2 : 1;           // B rows per output column
     constexpr uint32_t kSlot = (MIR == 4) ? kKS * 24 : kInSlotBytes;   // uv, w (, w2) per visibility
     // generator groups: one per stage of the ring at most (see kGroups)
-    constexpr int kGrp = kStages < kGroups ? kStages : kGroups;
+    constexpr int kGrp0 = kStages < kGroups ? kStages : kGroups;
+    // With two issuers the group count must be even: a group that waits for the release
+    // of stage s - S relies on its previous stage's wait (for stage s - kGrp - S) having
+    // seen stage s - 2S released, which only follows when both stages belong to the same
+    // issuer (each issuer commits in order, the two do not order each other).  An
+    // instance with five groups aliased the parity test and gave up its bounded waits.
+    constexpr int kGrp = (NISS == 2) ? (kGrp0 & ~1) : kGrp0;
+    static_assert(NISS == 1 || kGrp % 2 == 0, "two issuers need an even number of generator groups");
     static_assert(kGrp <= kStages, "generator groups must not exceed the operand ring depth");
     static_assert(!SPLIT || MIR <= 2, "split precision covers the plain and mirrored real-weight forms");
     // Two issuers take alternate stages; with an even ring depth every slot (and its release
