@@ -302,7 +302,8 @@ def measure_batched(psf, prec, steps=2, which="c4"):
         per[m] = {"ms": ms_m, "terms_per_s": K * bg.total_pixels() / (ms_m * 1e-3),
                   "kernel_ms": kms / steps, "kernel_launches_per_call": nkc / steps,
                   "algorithmic_flops_per_term": fpt, "kernel_tflops": tf,
-                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"]}
+                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"],
+                  "kernel_frac_of_sustained_peak": tf / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])}
         total_ms += ms_m
     ms = total_ms
     adj = None
@@ -350,7 +351,9 @@ def measure_batched(psf, prec, steps=2, which="c4"):
             plan.profile_enable(False)
             tf = 4.0 * K * len(sel) * N * N / (kms * 1e-3) / 1e12
             per_size[f"{N}px"] = {"positions": int(len(sel)), "kernel_ms": kms, "kernel_tflops": tf,
-                                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"]}
+                                  "kernel_frac_of_peak": tf / peaks["bf16_tflops"],
+                                  "kernel_frac_of_sustained_peak":
+                                      tf / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])}
     st = plan.sync_status()
     plan.close()
     if st != 0:
@@ -593,17 +596,21 @@ def measure_c5(psf, prec, nrad=128, nang=128):
     plan = psf.Plan(obs, prec=prec)
     torch.cuda.synchronize()
     plan_s = time.perf_counter() - t0
-    outs, ms = {}, {}
+    outs, ms, kms, nlaunch = {}, {}, {}, {}
     warm = psf.Batch(bg.lm[:256], N, bg.cell_rad)
     for m in ("exact", "uv", "img", "img_grid"):
         out = torch.empty(batch.total(), dtype=torch.float32, device="cuda")
         plan.forward(m, warm, out=out)                   # tuning, tables and warm-up
         torch.cuda.synchronize()
+        plan.profile_read()
+        plan.profile_enable(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         plan.forward(m, batch, out=out)
         e1.record()
         torch.cuda.synchronize()
+        kms[m], nlaunch[m], _ = plan.profile_read()
+        plan.profile_enable(False)
         ms[m] = e0.elapsed_time(e1)
         outs[m] = out.view(nrad, nang, N * N)
     eff = plan.exact(psf.Batch(np.zeros((1, 2)), N, bg.cell_rad)).view(1, 1, N * N)
@@ -647,11 +654,19 @@ def measure_c5(psf, prec, nrad=128, nang=128):
     if st != 0:
         raise RuntimeError("device-side wait timed out in the approximation workload")
     terms = K * bg.total_pixels()
+    peaks, _ = load_peaks()
+    # algorithmic flops per term: 4 with the complex weights of the exact method, 2 with real weights
+    tfl = {m: (4.0 if m == "exact" else 2.0) * terms / (kms[m] * 1e-3) / 1e12 for m in ("exact", "uv", "img")}
     uvm, imm = res["uv"]["err_max"], res["img"]["err_max"]
     return {"workload": "meerkat64_8km_4h_256ch_avg4_radial16384_64px", "nvis": K, "positions": bg.npos,
             "grid": f"{nrad} radii 3 deg (a+1)/{nrad} x {nang} position angles, 64 px at 1.5 arcsec",
             "precision": prec, "plan_build_s": plan_s,
             "ms": ms, "terms_per_s": {m: terms / (ms[m] * 1e-3) for m in ("exact", "uv", "img")},
+            "contraction": {m: {"kernel": "k_psf_kr", "ms": kms[m], "launches": int(nlaunch[m]),
+                                "tflops": tfl[m], "frac_of_peak": tfl[m] / peaks["bf16_tflops"],
+                                "frac_of_sustained_peak": tfl[m] / peaks.get("bf16_tflops_sustained",
+                                                                              peaks["bf16_tflops"])}
+                            for m in ("exact", "uv", "img")},
             "cost_ratio_exact_over": {m: ms["exact"] / ms[m] for m in ("uv", "img", "img_grid")},
             "err_vs_exact": {"uv_plane": res["uv"], "image_plane": res["img"], "image_plane_gridded": res["img_grid"],
                              "effective_psf_scaled_to_peak": res["effective"]},

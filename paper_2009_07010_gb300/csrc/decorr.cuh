@@ -88,7 +88,7 @@ __device__ __forceinline__ float sincpi_fast(float y) {
         const float x2 = x * x;
         return 1.0f + x2 * (-1.0f / 6.0f + x2 * (1.0f / 120.0f));
     }
-    return sinpi_fast(y) / x;
+    return __fdividef(sinpi_fast(y), x);   // |x| >= 0.1: the approximate quotient (2 ulp) suffices
 }
 __device__ __forceinline__ float dirichlet_fast(int F, float a) {
     if (F == 1) return 1.0f;
@@ -100,7 +100,7 @@ __device__ __forceinline__ float dirichlet_fast(int F, float a) {
         const float x2 = x * x, F2 = Ff * Ff;
         return sgn * (1.0f + x2 * ((1.0f - F2) / 6.0f + x2 * (7.0f / 360.0f - F2 / 36.0f + F2 * F2 / 120.0f)));
     }
-    return sgn * sinpi_fast(Ff * r) / (Ff * __sinf(x));
+    return sgn * __fdividef(sinpi_fast(Ff * r), Ff * __sinf(x));
 }
 
 // Uniform dispatch between the accurate and the fast forms.

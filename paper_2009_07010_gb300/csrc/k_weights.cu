@@ -167,8 +167,15 @@ __global__ void __launch_bounds__(256) k_weights16(DevObs o, int method, uint32_
     }
 }
 
-// Real weights (Methods 1 and 2): one FP16/BF16 value W_k D_k per visibility; a thread
-// owns the visibility pair (2 kp, 2 kp + 1) of a row (kpitch2 pairs per row).
+// Real weights (Methods 1 and 2, no windows): one FP16/BF16 value W_k D_k per
+// visibility; a thread owns the visibility pair (2 kp, 2 kp + 1) of a row (kpitch2 pairs
+// per row).  Both methods are D = sinc(A) sinc(B) with arguments that are, per
+// visibility, fixed forms in the position: Method 1 (Eq. 35) A = a . L and B = b . L
+// with a = (uvw(t_e) - uvw(t_s)) nu_r / c and b = ubar Dnu_r / c; Method 2 (Eqs. 38-44)
+// A = a . L with a = omega_E Dt (udot, vdot, 0) and B = f |(l0, m0)| with
+// f = (Dnu_r / nu_r) |(u, v)|.  The thread forms a, b, f once for its two visibilities
+// (decorr_uv / decorr_img do the same per call) and each position costs two dot
+// products and two sincs.
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, uint32_t flags,
                                                         const float4 *__restrict__ pos,
@@ -178,26 +185,52 @@ __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, ui
     const int32_t kp = blockIdx.x * blockDim.x + threadIdx.x;
     if (kp >= kpitch2) return;
     const int row0 = blockIdx.y * kRowsPerBlock;
-    int bin[2], rr[2];
+    float4 a[2], b[2];   // A = a . L; B = b . L (Method 1) or b.x |(l0, m0)| (Method 2)
     float Wk[2];
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
         const int32_t kk = 2 * kp + e;
         const bool valid = kk < kcn;
         const int32_t k = kc0 + (valid ? kk : 0);
-        bin[e] = k / o.nout;
-        rr[e] = k - bin[e] * o.nout;
+        const int bin = k / o.nout;
+        const int r = k - bin * o.nout;
         Wk[e] = valid ? o.W[k] : 0.f;
+        const float4 ub = o.bin_ubar[bin];
+        const float4 ch = o.chan[r];
+        if (method == kUV) {
+            const float4 ed = o.bin_edge[bin];
+            const float sa = ch.x * kInvC, sb = ch.y * kInvC;
+            a[e] = make_float4(ed.x * sa, ed.y * sa, ed.z * sa, 0.f);
+            b[e] = make_float4(ub.x * sb, ub.y * sb, ub.z * sb, 0.f);
+        } else {
+            const float sc = ch.x * kInvC;
+            const float u = ub.x * sc, v = ub.y * sc;
+            const float uvlen = sqrtf(u * u + v * v);
+            float udot = -v, vdot = u;
+            if (flags & PSF_IMG_LITERAL_THETA) {
+                const float th = (v != 0.0f) ? atanf(u / v) : (u >= 0.0f ? 0.5f * kPiF : -0.5f * kPiF);
+                float st, ct;
+                sincosf(th, &st, &ct);
+                udot = -uvlen * st;
+                vdot = uvlen * ct;
+            }
+            const float wdt = (float)kOmegaE * ub.w;
+            a[e] = make_float4(wdt * udot, wdt * vdot, 0.f, 0.f);
+            b[e] = make_float4(ch.y / ch.x * uvlen, 0.f, 0.f, 0.f);
+        }
     }
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int row = row0; row < min(rows, row0 + kRowsPerBlock); ++row) {
         const int slot = slot_of_row[row];
         float wv[2] = {0.f, 0.f};
         if (slot >= 0) {
             const float4 P = pos[slot];
+            const float rho = sqrtf(P.x * P.x + P.y * P.y);
 #pragma unroll
-            for (int e = 0; e < 2; ++e)
-                if (Wk[e] != 0.f) wv[e] = Wk[e] * decorr<false, true>(o, method, flags, bin[e], rr[e], P, z, z, nullptr).x;
+            for (int e = 0; e < 2; ++e) {
+                const float A = dot3(a[e], P);
+                const float B = (method == kUV) ? dot3(b[e], P) : b[e].x * rho;
+                if (Wk[e] != 0.f) wv[e] = Wk[e] * sincpi_fast(A) * sincpi_fast(B);
+            }
         }
         w16[(int64_t)row * kpitch2 + kp] = pack_sr<BF16>(wv[0], wv[1], sr_bits((uint32_t)slot, (uint32_t)(kc0 + 2 * kp)));
     }

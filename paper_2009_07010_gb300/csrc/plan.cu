@@ -568,7 +568,7 @@ int upload_meta(psf_plan_s *p, const void *src, size_t bytes, cudaStream_t st) {
 }
 
 constexpr size_t kWeightBudget = size_t(4) << 30;   // weights of one position chunk (bytes)
-constexpr size_t kW16Budget = size_t(1) << 30;      // FP16 weights of one batched chunk (bytes)
+constexpr size_t kW16Budget = size_t(4) << 30;      // FP16 weights of one batched chunk (bytes)
 constexpr int kKrMinGroup = 32;                     // positions of one size for the batched form
 
 // One size group of the batched form: positions idx (batch indices) of cutout size N.
