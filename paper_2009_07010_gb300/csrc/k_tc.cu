@@ -26,10 +26,11 @@
 //               TMEM accumulator while these warps read the first ones (tcgen05.ld),
 //               add them and add the sum into the CTA's FP32 partial tile in global
 //               memory.  Short TMEM accumulation runs bound the tensor-core rounding
-//               growth.  Each add into the running sum is an error-free TwoSum: its
-//               rounding error goes back into the drained accumulator, on which the
-//               issuer's next range in that buffer accumulates (compensated summation
-//               with the correction carried by the tensor core).
+//               growth.  In split precision each add into the running sum is an
+//               error-free TwoSum whose rounding error goes back into the drained
+//               accumulator, on which the issuer's next range in that buffer
+//               accumulates (compensated summation, the correction carried by the
+//               tensor core).
 // Stages are handed over with mbarriers (input copies -> generators: `in_full`,
 // generators -> input warp: `in_empty`, generators -> MMA: `full`, MMA commit ->
 // generators: `empty`, MMA commit -> drain: `acc_full`, drain -> MMA: `acc_empty`).
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // K' = 16 per MMA = 32 bytes (descriptor units of 16 B: +2) of the 128-byte row
                 // a range's first MMA clears the buffer, except issuer 0's from range 2 on:
                 // the drain has left the compensation of the running sum there
-                if (r == q) umma_f16(dt, ad, bd, idesc, (q == 0 && d >= 2) ? 1u : 0u);
+                if (r == q) umma_f16(dt, ad, bd, idesc, (SPLIT && q == 0 && d >= 2) ? 1u : 0u);
                 else umma_f16(dt, ad, bd, idesc, 1u);
                 umma_f16(dt, ad + 2, bd + 2, idesc, 1u);
                 umma_f16(dt, ad + 4, bd + 4, idesc, 1u);
@@ -604,9 +605,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int e = 0; e < 16; ++e) v[e] += v2[e];
                 }
-                float cv[16];   // compensation for the buffer's next range
                 if (SPLIT) {
-                    float sv[16];
+                    float sv[16], cv[16];   // running sum; compensation for the buffer's next range
 #pragma unroll
                     for (int e = 0; e < 16; ++e) sv[e] = 0.f;
                     if (d > 0) tmem_ld16(tsum + (uint32_t)c0, sv);
@@ -619,28 +619,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                         for (int e = 0; e < 16; ++e)
                             if (cb + e < ncol_valid) dd[(cb + e) * cstride] = v[e];
                     }
-                } else {
+                    // issuer 0's buffer b is accumulated on again by range d + 2
+                    if (d + 2 < ndrain) tmem_st16(ta + (uint32_t)c0, cv);
+                    continue;
+                }
+                if (row_ok) {
+                    // eight loads in flight before their stores (one L2 round trip per eight)
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) cv[e] = 0.f;
-                    if (row_ok) {
-                        // eight loads in flight before their stores (one L2 round trip per eight)
+                    for (int h = 0; h < 16; h += 8) {
+                        float o[8];
 #pragma unroll
-                        for (int h = 0; h < 16; h += 8) {
-                            float o[8];
+                        for (int e = 0; e < 8; ++e)
+                            o[e] = (d > 0 && cb + h + e < ncol_valid) ? dd[(cb + h + e) * cstride] : 0.f;
 #pragma unroll
-                            for (int e = 0; e < 8; ++e)
-                                o[e] = (d > 0 && cb + h + e < ncol_valid) ? dd[(cb + h + e) * cstride] : 0.f;
-#pragma unroll
-                            for (int e = 0; e < 8; ++e) {
-                                float t;
-                                two_sum(o[e], v[h + e], t, cv[h + e]);
-                                if (cb + h + e < ncol_valid) dd[(cb + h + e) * cstride] = t;
-                            }
-                        }
+                        for (int e = 0; e < 8; ++e)
+                            if (cb + h + e < ncol_valid) dd[(cb + h + e) * cstride] = o[e] + v[h + e];
                     }
                 }
-                // issuer 0's buffer b is accumulated on again by range d + 2
-                if (d + 2 < ndrain) tmem_st16(ta + (uint32_t)c0, cv);
             }
             tc_fence_before();
             __syncwarp();
