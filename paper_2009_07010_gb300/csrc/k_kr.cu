@@ -61,14 +61,29 @@ static_assert((2 * kKrStages + 2 * kKrIn + 3 + 5) * 8 + 2 * 4 + 8 <= 512, "barri
 
 // One 32-pixel run of one visibility (this lane): value(r) = exp(2 pi i (theta (n0 + r) + phi)),
 // r = 0..31, as eight interleaved 4-pixel pieces in packed FP32x2 recurrences.
+// The step phasor st = exp(2 pi i theta) and its 4-, 8- and 16-row strides depend only on
+// the visibility, so the caller forms them once per stage for all runs of its lane.
+struct Steps {
+    float2 st, s4, s8, s16;
+};
+__device__ __forceinline__ Steps make_steps(float theta) {
+    Steps S;
+    S.st = cis_turns(theta);
+    const float2 s2 = cmulf(S.st, S.st);
+    S.s4 = cmulf(s2, s2);
+    S.s8 = cmulf(S.s4, S.s4);
+    S.s16 = cmulf(S.s8, S.s8);
+    return S;
+}
+
 template <int BF16>
-__device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float phi) {
-    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3; two
-    // sine/cosine evaluations (row 0, step), piece seeds by the 4- and 16-row strides
-    const float2 st = cis_turns(theta);
+__device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float phi,
+                                          const Steps &S) {
+    // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3; one
+    // sine/cosine evaluation per run (row 0), piece seeds by the 4- and 16-row strides
+    const float2 st = S.st, s4 = S.s4, s8 = S.s8, s16 = S.s16;
     float2 z[8];
     z[0] = cis_turns(fmaf(theta, (float)n0, phi));
-    const float2 s2 = cmulf(st, st), s4 = cmulf(s2, s2), s8 = cmulf(s4, s4), s16 = cmulf(s8, s8);
     z[1] = cmulf(z[0], s4);
     z[2] = cmulf(z[0], s8);
     z[3] = cmulf(z[1], s8);
@@ -103,26 +118,38 @@ __device__ __forceinline__ void gen_run32(uint32_t base, const uint32_t (&off)[8
 // Real-weight form: lane t owns visibilities 2t and 2t+1 of a 64-visibility stage and
 // stores the pair (Re KR_2t, Re KR_2t+1) per pixel; the recurrences are packed across
 // the two visibilities, four interleaved 8-pixel pieces.
+struct StepsR {   // two visibilities: steps and their 8- and 16-row strides
+    float2 sa, sb, a8, a16, b8, b16;
+};
+__device__ __forceinline__ StepsR make_steps_real(float2 ta) {
+    StepsR S;
+    S.sa = cis_turns(ta.x);
+    S.sb = cis_turns(ta.y);
+    const float2 a2 = cmulf(S.sa, S.sa), a4 = cmulf(a2, a2);
+    const float2 b2 = cmulf(S.sb, S.sb), b4 = cmulf(b2, b2);
+    S.a8 = cmulf(a4, a4);
+    S.a16 = cmulf(S.a8, S.a8);
+    S.b8 = cmulf(b4, b4);
+    S.b16 = cmulf(S.b8, S.b8);
+    return S;
+}
+
 template <int BF16>
-__device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&off)[8], float2 ta, float2 tb,
-                                               int n0, float2 phi) {
+__device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&off)[8], float2 ta, int n0,
+                                               float2 phi, const StepsR &S) {
     // ta = (theta_u of visibility 2t, of 2t+1); phi likewise
     // piece seeds (rows 0, 8, 16, 24) from row 0 and the 8- and 16-row strides
-    // (squarings of the step): four sine/cosine evaluations per lane
-    const float2 sa = cis_turns(ta.x), sb = cis_turns(ta.y);
+    // (squarings of the step, formed by the caller): two sine/cosine evaluations per run
+    const float2 sa = S.sa, sb = S.sb;
     float2 za[4], zb[4];
     za[0] = cis_turns(fmaf(ta.x, (float)n0, phi.x));
     zb[0] = cis_turns(fmaf(ta.y, (float)n0, phi.y));
-    {
-        const float2 a2 = cmulf(sa, sa), a4 = cmulf(a2, a2), a8 = cmulf(a4, a4), a16 = cmulf(a8, a8);
-        const float2 b2 = cmulf(sb, sb), b4 = cmulf(b2, b2), b8 = cmulf(b4, b4), b16 = cmulf(b8, b8);
-        za[1] = cmulf(za[0], a8);
-        za[2] = cmulf(za[0], a16);
-        za[3] = cmulf(za[1], a16);
-        zb[1] = cmulf(zb[0], b8);
-        zb[2] = cmulf(zb[0], b16);
-        zb[3] = cmulf(zb[1], b16);
-    }
+    za[1] = cmulf(za[0], S.a8);
+    za[2] = cmulf(za[0], S.a16);
+    za[3] = cmulf(za[1], S.a16);
+    zb[1] = cmulf(zb[0], S.b8);
+    zb[2] = cmulf(zb[0], S.b16);
+    zb[3] = cmulf(zb[1], S.b16);
     float2 re[4], im[4];
 #pragma unroll
     for (int pc = 0; pc < 4; ++pc) {
@@ -130,7 +157,6 @@ __device__ __forceinline__ void gen_run32_real(uint32_t base, const uint32_t (&o
         im[pc] = make_float2(za[pc].y, zb[pc].y);
     }
     const float2 sr = make_float2(sa.x, sb.x), si = make_float2(sa.y, sb.y), nsi = make_float2(-sa.y, -sb.y);
-    (void)tb;
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         // rows q, q+8, q+16, q+24 = pieces 0..3 at step q
@@ -256,17 +282,21 @@ __global__ void __launch_bounds__(kKrThreads, 1)
                     w = wait_bounded(&empty[slot], ph ^ 1u, s_abort, err);
                     if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
                 }
+                Steps S;
+                StepsR SR;
+                if (REAL) SR = make_steps_real(make_float2(uva.x * cell, uvb.x * cell));
+                else S = make_steps(uva.x * cell);
                 for (int r0 = gw * 32; r0 < it.npx; r0 += kKrGroupWarps * 32) {   // 32-pixel runs of this warp
                     const int q = it.q0 + r0;
                     const int jrow = q / it.N, i0 = q - jrow * it.N;   // inside one cutout row
                     const uint32_t dst = smem_u32(b_base + slot * kKrBTile + r0 * 128);
                     if (REAL)
-                        gen_run32_real<BF16>(dst, off8, make_float2(uva.x * cell, uvb.x * cell), make_float2(0.f, 0.f),
-                                             i0 - half,
+                        gen_run32_real<BF16>(dst, off8, make_float2(uva.x * cell, uvb.x * cell), i0 - half,
                                              make_float2(uva.y * cell * (float)(jrow - half),
-                                                         uvb.y * cell * (float)(jrow - half)));
+                                                         uvb.y * cell * (float)(jrow - half)),
+                                             SR);
                     else
-                        gen_run32<BF16>(dst, off8, uva.x * cell, i0 - half, uva.y * cell * (float)(jrow - half));
+                        gen_run32<BF16>(dst, off8, uva.x * cell, i0 - half, uva.y * cell * (float)(jrow - half), S);
                 }
                 fence_proxy_async_smem();
                 __syncwarp();
