@@ -39,10 +39,44 @@ __global__ void __launch_bounds__(256) k_weights(DevObs o, int method, uint32_t 
     }
 }
 
+// Sums over the raw samples of one bin for the eight affine channels r0 .. r0 + 7 of a
+// thread: S_j = sum_s f_s exp(-2 pi i (nu_r0 + j dnu) ds_s / c), f_s the channel-
+// independent factor (the raw channels' Dirichlet kernel times their sinc, Eq. 13 with
+// a boxcar), held as packed FP32 pairs (S_j, S_j+4): per sample three phasors (j = 0,
+// j = 4 and the step) and three packed complex steps.
+__device__ __forceinline__ void exact8_sums(const DevObs &o, float4 ub, int2 sm, float4 ch, float4 L,
+                                            float2 (&re)[4], float2 (&im)[4]) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) { re[j] = make_float2(0.f, 0.f); im[j] = make_float2(0.f, 0.f); }
+    const float Xbar = dot3(ub, L);
+    for (int s = 0; s < sm.y; ++s) {
+        const float4 d = o.samp[sm.x + s];
+        const float ds = dot3(d, L);
+        const float Xs = Xbar + ds;
+        const float f = dirichlet_fast(o.favg, ch.z * Xs * kInvC) * sincpi_fast(ch.w * Xs * kInvC);
+        float es, ec, e4s, e4c, rs, rc;
+        sincospi2_fast(-ch.x * ds * kInvC, &es, &ec);
+        sincospi2_fast(-(ch.x + 4.0f * o.dnu_ch) * ds * kInvC, &e4s, &e4c);
+        sincospi2_fast(-o.dnu_ch * ds * kInvC, &rs, &rc);
+        float2 er = make_float2(ec * f, e4c * f), ei = make_float2(es * f, e4s * f);
+        const float2 rc2 = make_float2(rc, rc), rs2 = make_float2(rs, rs), nrs2 = make_float2(-rs, -rs);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            re[j] = __fadd2_rn(re[j], er);
+            im[j] = __fadd2_rn(im[j], ei);
+            if (j < 3) {
+                const float2 t = __fmul2_rn(ei, nrs2), u = __fmul2_rn(ei, rc2);
+                ei = __ffma2_rn(er, rs2, u);
+                er = __ffma2_rn(er, rc2, t);
+            }
+        }
+    }
+}
+
 // Exact-method weights of the tensor-core paths (FP32 (Re w, Im w) per position row,
 // MUFU sine/cosine after exact argument reduction) by the per-bin channel recurrence
 // of k_weights16_exact8: a thread owns eight consecutive channels of one bin, and per
-// raw sample two phasors and a complex recurrence replace eight phasors.
+// raw sample three phasors and a packed complex recurrence (exact8_sums) replace eight.
 __global__ void __launch_bounds__(256) k_weights_exact8(DevObs o, const float4 *__restrict__ pos, int32_t k0,
                                                         int32_t kn, float2 *__restrict__ w, int64_t ldw) {
     const int p = blockIdx.y;
@@ -55,34 +89,15 @@ __global__ void __launch_bounds__(256) k_weights_exact8(DevObs o, const float4 *
         const float4 ub = o.bin_ubar[bin];
         const int2 sm = o.bin_samp[bin];
         const float4 ch = o.chan[r0];
-        const float Xbar = dot3(ub, L);
-        float re[8], im[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
-        for (int s = 0; s < sm.y; ++s) {
-            const float4 d = o.samp[sm.x + s];
-            const float ds = dot3(d, L);
-            const float Xs = Xbar + ds;
-            const float f = dirichlet_fast(o.favg, ch.z * Xs * kInvC) * sincpi_fast(ch.w * Xs * kInvC);
-            float es, ec, rs, rc;
-            sincospi2_fast(-ch.x * ds * kInvC, &es, &ec);
-            sincospi2_fast(-o.dnu_ch * ds * kInvC, &rs, &rc);
-            float er = ec * f, ei = es * f;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                re[j] += er;
-                im[j] += ei;
-                const float t = er * rc - ei * rs;
-                ei = er * rs + ei * rc;
-                er = t;
-            }
-        }
+        float2 re[4], im[4];
+        exact8_sums(o, ub, sm, ch, L, re, im);
         const float inv = 1.0f / (float)sm.y;
         float2 *dst = w + (int64_t)p * ldw + kk0;
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
+            const float sr = (j < 4) ? re[j].x : re[j - 4].y, si = (j < 4) ? im[j].x : im[j - 4].y;
             const float Wk = (kk0 + j < kn) ? o.W[kb + j] : 0.f;
-            if (kk0 + j < kn) dst[j] = make_float2(Wk * re[j] * inv, Wk * im[j] * inv);
+            if (kk0 + j < kn) dst[j] = make_float2(Wk * sr * inv, Wk * si * inv);
         }
     }
 }
@@ -240,7 +255,8 @@ __global__ void __launch_bounds__(256) k_weights16_real(DevObs o, int method, ui
 // group count nout a multiple of 8).  Per raw sample only the factor
 // exp(-2 pi i nu_r ds / c) depends on the channel r; with nu_r = nu_r0 + j dnu it is
 // e0 rho^j, e0 = exp(-2 pi i nu_r0 ds / c), rho = exp(-2 pi i dnu ds / c), so a sample
-// costs two phasors and a recurrence instead of eight.  The channel-independent factor
+// costs three phasors (e0, e4 and rho) and a recurrence of packed FP32 pairs (channels j
+// and j + 4 together) instead of eight.  The channel-independent factor
 // is the Dirichlet kernel of the raw channels times their sinc (Eq. 13, boxcar).
 template <int BF16>
 __global__ void __launch_bounds__(256) k_weights16_exact8(DevObs o, uint32_t flags, const float4 *__restrict__ pos,
@@ -264,35 +280,19 @@ __global__ void __launch_bounds__(256) k_weights16_exact8(DevObs o, uint32_t fla
     const float inv = 1.0f / (float)sm.y;
     for (int row = row0; row < min(rows, row0 + kRowsPerBlock); ++row) {
         const int slot = slot_of_row[row];
-        float re[8], im[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) { re[j] = 0.f; im[j] = 0.f; }
+        // channels j and j + 4 as packed FP32 pairs: re[j] = (Re S_j, Re S_j+4), ...
+        float2 re[4], im[4];
         if (slot >= 0 && valid) {
-            const float4 L = pos[slot];
-            const float Xbar = dot3(ub, L);
-            for (int s = 0; s < sm.y; ++s) {
-                const float4 d = o.samp[sm.x + s];
-                const float ds = dot3(d, L);
-                const float Xs = Xbar + ds;
-                const float f = dirichlet_fast(o.favg, ch.z * Xs * kInvC) * sincpi_fast(ch.w * Xs * kInvC);
-                float es, ec, rs, rc;
-                sincospi2_fast(-ch.x * ds * kInvC, &es, &ec);
-                sincospi2_fast(-o.dnu_ch * ds * kInvC, &rs, &rc);
-                float er = ec * f, ei = es * f;
+            exact8_sums(o, ub, sm, ch, pos[slot], re, im);
+        } else {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    re[j] += er;
-                    im[j] += ei;
-                    const float t = er * rc - ei * rs;
-                    ei = er * rs + ei * rc;
-                    er = t;
-                }
-            }
+            for (int j = 0; j < 4; ++j) { re[j] = make_float2(0.f, 0.f); im[j] = make_float2(0.f, 0.f); }
         }
         uint32_t packed[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            const float wr = Wk[j] * re[j] * inv, wi = Wk[j] * im[j] * inv;
+            const float sr = (j < 4) ? re[j].x : re[j - 4].y, si = (j < 4) ? im[j].x : im[j - 4].y;
+            const float wr = Wk[j] * sr * inv, wi = Wk[j] * si * inv;
             packed[j] = pack_sr<BF16>(wr, -wi, sr_bits((uint32_t)slot, (uint32_t)(k0 + j)));
         }
         uint4 *dst = reinterpret_cast<uint4 *>(w16 + (int64_t)row * kpitch + kk0);

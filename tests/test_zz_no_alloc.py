@@ -99,3 +99,28 @@ def test_noalloc_meerkat_cutout(lib):
         assert plan.sync_status() == 0
     ref = oracle.psf(obs, oracle.EXACT, batch, pix_sel=sel)
     assert _err(got[sel], ref[sel]) <= 1e-6, _err(got[sel], ref[sel])
+
+
+def test_noalloc_leaves_device_memory_untouched(lib):
+    """After a first call (which looks up the scratch array), further calls change the
+    device's free memory by nothing: no allocation by the library, the CUDA runtime or
+    the driver on its behalf (an allocation is granular to at least 2 MB, so the free
+    byte count would move).  The output buffer is allocated before the measurement."""
+    import torch
+    psf, _lib, L = lib
+    obs = obsgen.config1_obs()
+    cell = obsgen.ARCSEC * 2.0
+    N = 128
+    with psf.Plan(obs, prec="fp32") as plan:
+        out = torch.empty(N * N, device="cuda")
+        stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        assert L.psf_exact_noalloc(plan._h, 0.01, -0.02, N, cell, ctypes.c_void_p(out.data_ptr()), stream) == 0
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for i in range(5):
+            l0 = 0.005 * (i + 1)
+            assert L.psf_exact_noalloc(plan._h, l0, -l0, N, cell, ctypes.c_void_p(out.data_ptr()), stream) == 0
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
+        assert plan.sync_status() == 0
