@@ -571,7 +571,7 @@ def measure_fwhm(psf, prec):
             "positions": bg.npos, **out}
 
 
-def measure_c5(psf, prec, nrad=128, nang=128):
+def measure_c5(psf, prec, nrad=128, nang=128, ref="fp16"):
     """Approximations against the exact smeared PSF on the approximation workload (64-antenna
     8 km array, 4 h of 1 s samples averaged 8:1, 256 channels of 3.34375 MHz averaged 4:1 ->
     232 243 200 visibilities; 64 x 64 cutouts at 1.5" on the radial grid of nrad radii to 3
@@ -614,14 +614,32 @@ def measure_c5(psf, prec, nrad=128, nang=128):
         ms[m] = e0.elapsed_time(e1)
         outs[m] = out.view(nrad, nang, N * N)
     eff = plan.exact(psf.Batch(np.zeros((1, 2)), N, bg.cell_rad)).view(1, 1, N * N)
-    ex = outs["exact"]
+    ref_ms = None
+    if ref == "bf16x3":
+        # the map reference: the exact PSF of every position in the split mode BF16X3
+        # (per-cutout form, ~3e-6 of the peak), in chunks of 1024 positions
+        plan.set_opts(prec="tc_bf16x3")
+        ex = torch.empty(nrad * nang, N * N, dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for c0 in range(0, nrad * nang, 1024):
+            lmc = bg.lm[c0:c0 + 1024]
+            plan.exact(psf.Batch(lmc, N, bg.cell_rad), out=ex[c0:c0 + len(lmc)].view(-1))
+        e1.record()
+        torch.cuda.synchronize()
+        ref_ms = e0.elapsed_time(e1)
+        plan.set_opts(prec=prec)
+        ex = ex.view(nrad, nang, N * N)
+    else:
+        ex = outs["exact"]
     peak = ex.abs().amax(dim=2)                                          # [nrad, nang]
     outs["effective"] = eff / eff.abs().max() * peak.unsqueeze(-1)
     radius = 3.0 * (np.arange(nrad) + 1) / nrad
     picks = sorted(set([0, 1, 3, 7, 11] + list(range(15, nrad, 16)) + [nrad - 1]))
     key = [f"{radius[i]:.4f}deg" for i in range(nrad)]
     res = {}
-    for m in ("uv", "img", "img_grid", "effective"):
+    for m in ("uv", "img", "img_grid", "effective") + (("exact",) if ref == "bf16x3" else ()):
         d = outs[m] - ex
         emax = (d.abs().amax(dim=2) / peak).amax(dim=1).cpu().numpy()                 # worst angle per radius
         erms = ((d * d).mean(dim=2).sqrt() / peak).amax(dim=1).cpu().numpy()
@@ -668,8 +686,11 @@ def measure_c5(psf, prec, nrad=128, nang=128):
                                                                               peaks["bf16_tflops"])}
                             for m in ("exact", "uv", "img")},
             "cost_ratio_exact_over": {m: ms["exact"] / ms[m] for m in ("uv", "img", "img_grid")},
+            "map_reference": ("exact PSF in BF16X3 for every position (per-cutout form), %.1f s" % (ref_ms / 1e3)
+                              if ref == "bf16x3" else "exact PSF in the batched %s form" % prec),
             "err_vs_exact": {"uv_plane": res["uv"], "image_plane": res["img"], "image_plane_gridded": res["img_grid"],
-                             "effective_psf_scaled_to_peak": res["effective"]},
+                             "effective_psf_scaled_to_peak": res["effective"],
+                             **({"exact_batched_" + prec: res["exact"]} if ref == "bf16x3" else {})},
             "finer_reference": {"what": "exact PSF in BF16X3 (per-cutout form), every radius x 2 angles",
                                 "positions": int(len(lm_f)), "ms": fine_ms,
                                 "err_max_vs_bf16x3_exact": fine_res},
@@ -693,6 +714,9 @@ def main():
     ap.add_argument("--no-facets", action="store_true")
     ap.add_argument("--no-ladder", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--c5-ref", default="fp16", choices=["fp16", "bf16x3"],
+                    help="map reference of the approximation workload: the batched exact PSF in the plan's "
+                         "precision (default) or the BF16X3 exact PSF of all 16 384 positions (about 15 min)")
     ap.add_argument("--grid-positions", type=int, default=16384,
                     help="positions of the gridded-form measurement (radial grid out to 3 deg)")
     ap.add_argument("--workload", default="c2", choices=["c2", "c2_1h", "c3", "c4", "c5", "grid", "clean", "facets"],
@@ -747,7 +771,7 @@ def main():
         import paper_2009_07010_gb300 as psf
         psf.build_library()
         torch.cuda.set_device(local)
-        print(json.dumps(measure_c5(psf, args.prec)), flush=True)
+        print(json.dumps(measure_c5(psf, args.prec, ref=args.c5_ref)), flush=True)
         return 0
 
     import torch
