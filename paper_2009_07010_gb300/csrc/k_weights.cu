@@ -500,6 +500,61 @@ cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, cons
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------------- binning (plan build)
+// One thread per averaging bin: baseline b (binary search in bin_first), bin tau of its
+// tavg[b] raw samples s0 = tau tavg[b] ...  Eq. 12's bin centre is the mean of the raw
+// uvw, summed in sample order in float64 and divided by n; the edge delta (Eq. 33) is
+// uvw(last) - uvw(first) scaled by n / (n - 1) (the bin's full width), or for a single
+// sample the central difference of the neighbouring samples; the raw samples are kept as
+// float32 offsets from the centre.  The same float64 operations in the same order as a
+// host loop, so the records are bit-identical to host binning.
+__global__ void __launch_bounds__(256) k_bin(const double *__restrict__ uvw, int ntime, int nbl,
+                                             const int32_t *__restrict__ tavg, const int32_t *__restrict__ bin_first,
+                                             const int64_t *__restrict__ samp_first, double dt_raw,
+                                             float4 *__restrict__ bin_ubar, double2 *__restrict__ bin_uv64,
+                                             float4 *__restrict__ bin_edge, int2 *__restrict__ bin_samp,
+                                             float4 *__restrict__ samp) {
+    const int32_t bin = blockIdx.x * blockDim.x + threadIdx.x;
+    if (bin >= bin_first[nbl]) return;
+    int lo = 0, hi = nbl;   // bin_first[lo] <= bin < bin_first[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bin_first[mid] <= bin) lo = mid; else hi = mid;
+    }
+    const int b = lo, n = tavg[b];
+    const int64_t tau = bin - bin_first[b];
+    const int64_t s0 = tau * n;
+    const double *ub = uvw + (size_t)b * ntime * 3;
+    double mean[3] = {0, 0, 0}, edge[3] = {0, 0, 0};
+    for (int64_t s = s0; s < s0 + n; ++s)
+        for (int d = 0; d < 3; ++d) mean[d] += ub[s * 3 + d];
+    for (int d = 0; d < 3; ++d) mean[d] /= n;
+    if (n >= 2) {
+        for (int d = 0; d < 3; ++d) edge[d] = __dmul_rn(ub[(s0 + n - 1) * 3 + d] - ub[s0 * 3 + d], (double)n) / (double)(n - 1);
+    } else if (ntime >= 2) {
+        const int64_t sa = s0 > 0 ? s0 - 1 : s0, sb = s0 < ntime - 1 ? s0 + 1 : s0;
+        for (int d = 0; d < 3; ++d) edge[d] = (ub[sb * 3 + d] - ub[sa * 3 + d]) / (double)(sb - sa);
+    }
+    const int64_t rec = samp_first[b] + tau * n;
+    bin_ubar[bin] = make_float4((float)mean[0], (float)mean[1], (float)mean[2], (float)(n * dt_raw));
+    bin_uv64[bin] = make_double2(mean[0], mean[1]);
+    bin_edge[bin] = make_float4((float)edge[0], (float)edge[1], (float)edge[2], 0.f);
+    bin_samp[bin] = make_int2((int)rec, n);
+    for (int s = 0; s < n; ++s) {
+        const double *u = ub + (s0 + s) * 3;
+        samp[rec + s] = make_float4((float)(u[0] - mean[0]), (float)(u[1] - mean[1]), (float)(u[2] - mean[2]), 0.f);
+    }
+}
+
+cudaError_t launch_bin(const double *uvw, int ntime, int nbl, const int32_t *tavg, const int32_t *bin_first,
+                       const int64_t *samp_first, int64_t nbin, double dt_raw, float4 *bin_ubar, double2 *bin_uv64,
+                       float4 *bin_edge, int2 *bin_samp, float4 *samp, cudaStream_t st) {
+    if (nbin <= 0) return cudaSuccess;
+    k_bin<<<(unsigned)((nbin + 255) / 256), 256, 0, st>>>(uvw, ntime, nbl, tavg, bin_first, samp_first, dt_raw,
+                                                           bin_ubar, bin_uv64, bin_edge, bin_samp, samp);
+    return cudaGetLastError();
+}
+
 // --------------------------------------------------------------- per-visibility tables
 // uv[k] + uv_lo[k] = ubar (x, y) nu_r / c in wavelengths, formed in float64 from the bin
 // means and channel frequencies and split into a rounded float pair; W[k] = tavg * favg

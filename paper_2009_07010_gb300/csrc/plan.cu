@@ -20,7 +20,6 @@
 #include <map>
 #include <memory>
 #include <new>
-#include <thread>
 #include <vector>
 
 #include "psf_internal.cuh"
@@ -182,21 +181,6 @@ int validate_opts(const psf_opts_t *op) {
     return PSF_OK;
 }
 
-template <class F>
-void parallel_for(int64_t n, F f) {
-    unsigned nt = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-    if (n < 64 || nt == 1) {
-        for (int64_t i = 0; i < n; ++i) f(i);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (unsigned t = 0; t < nt; ++t)
-        th.emplace_back([&, t] {
-            for (int64_t i = t; i < n; i += nt) f(i);
-        });
-    for (auto &x : th) x.join();
-}
-
 }  // namespace
 
 extern "C" {
@@ -245,49 +229,18 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
         return fail(PSF_ECUDA);
     }
 
-    // ---- float64 binning on the host, float32 records out
+    // ---- channel records on the host (a few per output channel); the averaging bins are
+    // formed on the device from the raw uvw (k_bin), float64 in, float32 records out
     const double dt = o->ntime >= 2 ? (o->time_s[o->ntime - 1] - o->time_s[0]) / (o->ntime - 1) : 0.0;
-    std::vector<float4> h_ubar, h_edge, h_samp, h_chan, h_raw;
-    std::vector<int2> h_bs;
-    std::vector<double2> h_uv64, h_chan64;
+    std::vector<float4> h_chan, h_raw;
+    std::vector<double2> h_chan64;
     std::vector<int32_t> h_bf;
     try {
-        h_ubar.resize(nbin); h_edge.resize(nbin); h_bs.resize(nbin); h_samp.resize(nsamp);
         h_chan.resize(nout); h_raw.resize((size_t)o->nchan);
-        h_uv64.resize(nbin); h_chan64.resize(nout); h_bf.resize(o->nbl + 1);
+        h_chan64.resize(nout); h_bf.resize(o->nbl + 1);
     } catch (...) {
         return fail(PSF_ENOMEM);
     }
-    parallel_for(o->nbl, [&](int64_t b) {
-        const int n = o->tavg[b];
-        const double *ub = o->uvw_m + (size_t)b * o->ntime * 3;
-        const int64_t nb = bin_first[b + 1] - bin_first[b];
-        for (int64_t tau = 0; tau < nb; ++tau) {
-            const int64_t s0 = tau * n;
-            double mean[3] = {0, 0, 0}, edge[3] = {0, 0, 0};
-            for (int64_t s = s0; s < s0 + n; ++s)
-                for (int d = 0; d < 3; ++d) mean[d] += ub[s * 3 + d];
-            for (int d = 0; d < 3; ++d) mean[d] /= n;
-            if (n >= 2) {
-                for (int d = 0; d < 3; ++d)
-                    edge[d] = (ub[(s0 + n - 1) * 3 + d] - ub[s0 * 3 + d]) * (double)n / (double)(n - 1);
-            } else if (o->ntime >= 2) {
-                const int64_t sa = s0 > 0 ? s0 - 1 : s0, sb = s0 < o->ntime - 1 ? s0 + 1 : s0;
-                for (int d = 0; d < 3; ++d) edge[d] = (ub[sb * 3 + d] - ub[sa * 3 + d]) / (double)(sb - sa);
-            }
-            const int64_t bin = bin_first[b] + tau;
-            const int64_t rec = samp_first[b] + tau * n;
-            h_ubar[bin] = make_float4((float)mean[0], (float)mean[1], (float)mean[2], (float)(n * dt));
-            h_uv64[bin] = make_double2(mean[0], mean[1]);
-            h_edge[bin] = make_float4((float)edge[0], (float)edge[1], (float)edge[2], 0.f);
-            h_bs[bin] = make_int2((int)rec, n);
-            for (int64_t s = 0; s < n; ++s) {
-                const double *u = ub + (s0 + s) * 3;
-                h_samp[rec + s] = make_float4((float)(u[0] - mean[0]), (float)(u[1] - mean[1]),
-                                              (float)(u[2] - mean[2]), 0.f);
-            }
-        }
-    });
     if (nsamp >= (int64_t(1) << 31)) return fail(PSF_EUNSUPPORTED);
     int uniform = 1;
     for (int r = 0; r < nout; ++r) {
@@ -307,23 +260,41 @@ int psf_plan(const psf_obs_t *o, const psf_opts_t *opts, psf_plan_t *out) {
         h_chan64[r] = make_double2(nu, dnu);
     }
 
-    // ---- device copies
+    // ---- device copies and the binning
     cudaError_t e = cudaSuccess;
 #define UP(buf, vec)                                                                               \
     if (e == cudaSuccess) e = p->buf.reserve(std::max<size_t>(16, vec.size() * sizeof(vec[0])));   \
     if (e == cudaSuccess && !vec.empty())                                                          \
         e = cudaMemcpy(p->buf.p, vec.data(), vec.size() * sizeof(vec[0]), cudaMemcpyHostToDevice);
-    UP(bin_ubar, h_ubar)
-    UP(bin_edge, h_edge)
-    UP(bin_samp, h_bs)
-    UP(samp, h_samp)
     UP(chan, h_chan)
     UP(rawchan, h_raw)
     for (int b = 0; b <= o->nbl; ++b) h_bf[b] = (int32_t)bin_first[b];
-    UP(bin_uv64, h_uv64)
     UP(chan64, h_chan64)
     UP(bin_first, h_bf)
 #undef UP
+    if (e == cudaSuccess) e = p->bin_ubar.reserve((size_t)nbin * sizeof(float4));
+    if (e == cudaSuccess) e = p->bin_edge.reserve((size_t)nbin * sizeof(float4));
+    if (e == cudaSuccess) e = p->bin_samp.reserve((size_t)nbin * sizeof(int2));
+    if (e == cudaSuccess) e = p->bin_uv64.reserve((size_t)nbin * sizeof(double2));
+    if (e == cudaSuccess) e = p->samp.reserve((size_t)nsamp * sizeof(float4));
+    {
+        // the raw uvw, tavg and sample offsets live on the device for the binning only
+        DevBuf d_uvw, d_tavg, d_sfirst;
+        const size_t uvw_bytes = (size_t)o->nbl * o->ntime * 3 * sizeof(double);
+        if (e == cudaSuccess) e = d_uvw.reserve(uvw_bytes);
+        if (e == cudaSuccess) e = d_tavg.reserve((size_t)o->nbl * sizeof(int32_t));
+        if (e == cudaSuccess) e = d_sfirst.reserve((size_t)(o->nbl + 1) * sizeof(int64_t));
+        if (e == cudaSuccess) e = cudaMemcpy(d_uvw.p, o->uvw_m, uvw_bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d_tavg.p, o->tavg, (size_t)o->nbl * sizeof(int32_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(d_sfirst.p, samp_first.data(), (size_t)(o->nbl + 1) * sizeof(int64_t), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_bin((const double *)d_uvw.p, o->ntime, o->nbl, (const int32_t *)d_tavg.p,
+                           (const int32_t *)p->bin_first.p, (const int64_t *)d_sfirst.p, nbin, dt,
+                           (float4 *)p->bin_ubar.p, (double2 *)p->bin_uv64.p, (float4 *)p->bin_edge.p,
+                           (int2 *)p->bin_samp.p, (float4 *)p->samp.p, 0);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();   // before the temporaries are freed
+    }
     p->dt_raw = dt;
     try {
         p->h_tavg.assign(o->tavg, o->tavg + o->nbl);

@@ -71,6 +71,10 @@ cudaError_t launch_reduce(const float *partial, int nsplit, int64_t stride, cons
                           cudaStream_t st);
 // Plan-time per-visibility tables: uv[k] + uv_lo[k] (from the float64 bin means and
 // channel frequencies) and, if natural, W[k] = tavg * favg.
+// Averaging bins of the plan from the raw uvw on the device (k_weights.cu, k_bin).
+cudaError_t launch_bin(const double *uvw, int ntime, int nbl, const int32_t *tavg, const int32_t *bin_first,
+                       const int64_t *samp_first, int64_t nbin, double dt_raw, float4 *bin_ubar, double2 *bin_uv64,
+                       float4 *bin_edge, int2 *bin_samp, float4 *samp, cudaStream_t st);
 cudaError_t launch_fill_vis(const DevObs &o, const double2 *bin_uv64, const double2 *chan64, float2 *uv,
                             float2 *uv_lo, float *W, int natural, cudaStream_t st);
 // Adjoint (vector-Jacobian product) in FP32, see psf_adjoint (k_adjoint.cu).
