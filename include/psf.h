@@ -154,9 +154,11 @@ typedef struct {
     const int64_t *out_offset;
 } psf_batch_t;
 
-/* Build a plan: bins raw samples (Eq. 12), forms bin centres and bin-edge deltas
- * (Eqs. 31-33) in float64 on the host, rounds them to float32 and copies them to
- * the current device.  Position independent; done once per observation.
+/* Build a plan: copies the raw uvw (host memory, float64) to the current device, bins
+ * the raw samples there (Eq. 12), forms bin centres and bin-edge deltas (Eqs. 31-33) in
+ * float64 and keeps them as float32 records, with the per-visibility tables, on the
+ * device.  Position independent; done once per observation.  Synchronous; the temporary
+ * device copy of the uvw (nbl x ntime x 24 bytes) is freed before the call returns.
  * Returns PSF_EINVAL for inconsistent sizes/NULL arrays/non-uniform time steps,
  * PSF_ENOMEM / PSF_ECUDA on allocation or copy failure.  *out is set on success
  * and must be released with psf_plan_destroy. */
