@@ -897,9 +897,10 @@ def main():
     clean = None if args.no_clean or rank != 0 else measure_clean(psf, plan)
     fwhm = None if args.no_fwhm or rank != 0 else measure_fwhm(psf, args.prec)
     facets = None if args.no_facets or rank != 0 else measure_facets(psf, plan)
-    batched = None if args.no_batched else measure_batched(psf, args.prec)
-    batched_c3 = None if args.no_batched else measure_batched(psf, args.prec, steps=1, which="c3")
-    c5 = None if args.no_c5 or rank != 0 else measure_c5(psf, args.prec)
+    # side measurements on rank 0 only; the approximation workload (minutes) with one GPU only
+    batched = None if args.no_batched or rank != 0 else measure_batched(psf, args.prec)
+    batched_c3 = None if args.no_batched or rank != 0 else measure_batched(psf, args.prec, steps=1, which="c3")
+    c5 = None if args.no_c5 or rank != 0 or world > 1 else measure_c5(psf, args.prec)
     parity = None if (args.no_cpu_baseline or rank != 0) else parity_check(psf)
 
     if rank == 0:
