@@ -21,6 +21,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -172,6 +173,7 @@ def run_reference(args, rank, world):
             "dtype": "f64", "data": "synthetic",
             "config": step_config(args, K, N),
             "cpu_baseline": {"value": val, "unit": "terms/s", "cores": cores, "kind": "oracle",
+                             "host": f"{platform.machine()}, {os.cpu_count()} logical CPUs",
                              "sample": f"{npx} random pixels per method of the 128x128 cutout, all {K} visibilities"},
             "e2e": {"value": val, "unit": "terms/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -253,13 +255,14 @@ def cpu_baseline_sample(obs, batch):
     import oracle
     K = obs.nvis()
     N = int(batch.npix[0])
-    npx = 16
+    npx = 96
     sel = np.sort(np.random.default_rng(3).choice(N * N, npx, replace=False))
     t0 = time.perf_counter()
     oracle.psf(obs, oracle.EXACT, batch, pix_sel=sel)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
     return {"value": npx * K / dt, "unit": "terms/s", "cores": cores, "kind": "oracle",
+            "host": f"{platform.machine()}, {os.cpu_count()} logical CPUs",
             "sample": f"exact method, {npx} random pixels of the 128x128 cutout over all {K} visibilities "
                       f"({dt:.1f} s incl. the oracle's binning and decorrelation pass)"}
 
