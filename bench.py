@@ -580,13 +580,15 @@ def measure_c5(psf, prec, nrad=128, nang=128, ref="fp16"):
     232 243 200 visibilities; 64 x 64 cutouts at 1.5" on the radial grid of nrad radii to 3
     deg x nang position angles, 16 384 positions).  Every map is computed on the GPU in one
     batched call per method: the exact PSF (FP16 operands, FP32 accumulation; the map
-    reference), Method 1 (uv), Method 2 (img), Method 2 in the gridded form of Eq. 45
+    reference unless ref="bf16x3", which evaluates the exact PSF of every position in the
+    split mode BF16X3 as the reference, about 14 minutes), Method 1 (uv), Method 2 (img),
+    Method 2 in the gridded form of Eq. 45
     (img_grid; its position-independent table is built by a first call outside the timing)
     and the effective PSF (the phase-centre cutout, scaled to each position's peak).  Per
     radius: the largest over the angles of the peak-normalised max and RMS error, and the
     max in dB (10 log10 |P - P_ref| of the normalised PSFs).  The reference's own error is
     measured at 256 positions (every radius, 2 angles) against the exact PSF in the split
-    mode BF16X3 (per-cutout form, about 1e-6); the approximations are also compared with
+    mode BF16X3 (per-cutout form, about 3e-6); the approximations are also compared with
     that finer reference there.  tests/test_c5_gpu.py ties these paths to the FP64 oracle.
     Cost ratios t_exact / t_approx from the same engine."""
     import torch
