@@ -267,7 +267,7 @@ def cpu_baseline_sample(obs, batch):
                       f"({dt:.1f} s incl. the oracle's binning and decorrelation pass)"}
 
 
-def measure_batched(psf, prec, steps=2, which="c4"):
+def measure_batched(psf, prec, steps=2, which="c4", profile_range=False):
     """Batched form on the differentiation workload (c4: 256 positions, 64 x 64
     cutouts) or the batched-positions workload (c3: 4096 positions within 2 degrees,
     sizes drawn from 32..256); both on the baseline-dependent-averaging observation
@@ -292,12 +292,16 @@ def measure_batched(psf, prec, steps=2, which="c4"):
         torch.cuda.synchronize()
         plan.profile_read()
         plan.profile_enable(True)
+        if profile_range:   # the timed calls only, for ncu --profile-from-start off
+            torch.cuda.profiler.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(steps):
             plan.forward(m, batch, out=out)
         e1.record()
         torch.cuda.synchronize()
+        if profile_range:
+            torch.cuda.profiler.stop()
         ms_m = e0.elapsed_time(e1) / steps
         kms, nkc, _ = plan.profile_read()
         plan.profile_enable(False)
@@ -719,6 +723,9 @@ def main():
     ap.add_argument("--no-facets", action="store_true")
     ap.add_argument("--no-ladder", action="store_true")
     ap.add_argument("--no-c5", action="store_true")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="c3 / c4: bracket the timed calls with cudaProfilerStart/Stop (for ncu "
+                         "--profile-from-start off)")
     ap.add_argument("--c5-ref", default="fp16", choices=["fp16", "bf16x3"],
                     help="map reference of the approximation workload: the batched exact PSF in the plan's "
                          "precision (default) or the BF16X3 exact PSF of all 16 384 positions (about 15 min)")
@@ -739,7 +746,8 @@ def main():
         import paper_2009_07010_gb300 as psf
         psf.build_library()
         torch.cuda.set_device(local)
-        print(json.dumps(measure_batched(psf, args.prec, steps=args.steps, which=args.workload)), flush=True)
+        print(json.dumps(measure_batched(psf, args.prec, steps=args.steps, which=args.workload,
+                                         profile_range=args.profile_range)), flush=True)
         return 0
     if args.workload == "clean":
         import torch
