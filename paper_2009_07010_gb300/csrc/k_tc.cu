@@ -101,19 +101,33 @@ constexpr int kATileBytes = 128 * 128;
 // SPLIT: every value is also written as its low part (value - rounded value, rounded
 // to 16 bits) at the same position lo_off bytes further on (the lo tile of a split
 // precision stage); conjugation of the low part is the same sign-bit XOR.
+// The step exp(2 pi i theta) of a chain and its 4-, 8- and 16-row strides (squarings):
+// shared by the chains of one visibility that have the same theta.
+struct ChainSteps {
+    float2 st, s4, s8, s16;
+};
+__device__ __forceinline__ ChainSteps chain_steps(float theta) {
+    ChainSteps S;
+    S.st = cis_turns(theta);
+    const float2 s2 = cmulf(S.st, S.st);
+    S.s4 = cmulf(s2, s2);
+    S.s8 = cmulf(S.s4, S.s4);
+    S.s16 = cmulf(S.s8, S.s8);
+    return S;
+}
+
 template <int BF16, bool MIRROR = false, bool CPLX = false, bool SPLIT = false>
-__device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float2 wk,
-                                            bool weighted, uint32_t mbase = 0, bool tail = false,
-                                            uint32_t tail_addr = 0, uint32_t lo_off = 0) {
+__device__ __forceinline__ void gen_chain32_s(const ChainSteps &S, uint32_t base, const uint32_t (&off)[8],
+                                              float theta, int n0, float2 wk, bool weighted, uint32_t mbase = 0,
+                                              bool tail = false, uint32_t tail_addr = 0, uint32_t lo_off = 0) {
     // eight interleaved 4-row pieces: rows q + 4p (p = 0..7) at step q = 0..3.  Two
-    // sine/cosine evaluations per chain (row 0 and the step); the piece seeds follow
-    // by complex multiplication with the 4- and 16-row strides (squarings of the
-    // step), which keeps the MUFU pipe to 4 instructions per 32 rows.
-    const float2 st = cis_turns(theta);
+    // sine/cosine evaluations per chain (row 0 and the step, the latter in S); the piece
+    // seeds follow by complex multiplication with the 4- and 16-row strides (squarings
+    // of the step), which keeps the MUFU pipe to 4 instructions per 32 rows.
+    const float2 st = S.st, s4 = S.s4, s8 = S.s8, s16 = S.s16;
     float2 z[8];
     z[0] = cis_turns(theta * (float)n0);
     if (weighted) z[0] = cmulf(z[0], wk);
-    const float2 s2 = cmulf(st, st), s4 = cmulf(s2, s2), s8 = cmulf(s4, s4), s16 = cmulf(s8, s8);
     z[1] = cmulf(z[0], s4);
     z[2] = cmulf(z[0], s8);
     z[3] = cmulf(z[1], s8);
@@ -208,6 +222,14 @@ __device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)
                          "r"(pack2_lo<BF16>(r32, -i32, h))
                          : "memory");
     }
+}
+
+template <int BF16, bool MIRROR = false, bool CPLX = false, bool SPLIT = false>
+__device__ __forceinline__ void gen_chain32(uint32_t base, const uint32_t (&off)[8], float theta, int n0, float2 wk,
+                                            bool weighted, uint32_t mbase = 0, bool tail = false,
+                                            uint32_t tail_addr = 0, uint32_t lo_off = 0) {
+    gen_chain32_s<BF16, MIRROR, CPLX, SPLIT>(chain_steps(theta), base, off, theta, n0, wk, weighted, mbase, tail,
+                                             tail_addr, lo_off);
 }
 
 // Two real-weight copies of one conjugate-symmetric 32-row chain of unweighted twiddles
@@ -429,6 +451,26 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             const uint32_t a_tile = smem_u32(smem + L.a_off + slot * kAStage);
             const uint32_t b_tile = smem_u32(smem + L.b_off + slot * b_stage);
+            if (MIR == 0 && !SPLIT && nA == 4 && nB == 4) {
+                // complex weights on a full 128 x 128 tile: warps 0-1 take two A chains each
+                // (rows 64 gw .. 64 gw + 63), warps 2-3 two B chains each, so the two chains
+                // of a warp share one theta and its step phasors
+                const bool isA = gw < 2;
+                const int c0 = 2 * (gw & 1);
+                const float th = isA ? uvk.y * cell : -uvk.x * cell;
+                const ChainSteps S = chain_steps(th);
+#pragma unroll 1
+                for (int c = c0; c < c0 + 2; ++c) {
+                    if (isA)
+                        gen_chain32_s<BF16, false, false, SPLIT>(S, a_tile + c * 32 * 128, off8, th,
+                                                                 it.j0 + c * 32 - half, wk, true, 0, false, 0,
+                                                                 (uint32_t)kATileBytes);
+                    else
+                        gen_chain32_s<BF16, false, false, SPLIT>(S, b_tile + c * 32 * 128, off8, th,
+                                                                 it.i0 + c * 32 - half, wk, false, 0, false, 0,
+                                                                 bt_stride);
+                }
+            } else
             for (int ch = gw; ch < nA + nB; ch += kGroupWarps) {
                 if (MIR == 5) {   // A: weighted column twiddles; B: row twiddles, real and imaginary halves
                     if (ch < nA)
