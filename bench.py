@@ -40,8 +40,8 @@ FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustain
 # profiles/k_psf_tc_meerkat64_1h_128px.md, per visibility (traffic is proportional to
 # K; the mean of the step's two launches: exact, fused uv + img), valid only for the
 # kernel source it was taken on.
-PROFILED_TRAFFIC = {"kernel_sha256_prefix": "4f9bd1f02ab95af3",
-                    "bytes_per_vis": ((232.667648e6 + 3.815168e6) + (348.590080e6 + 4.414720e6)) / 2 / 14515200,
+PROFILED_TRAFFIC = {"kernel_sha256_prefix": "86620fd584ed55e3",
+                    "bytes_per_vis": ((232.290816e6 + 3.294976e6) + (348.522496e6 + 0.410368e6)) / 2 / 14515200,
                     "profile": "profiles/k_psf_tc_meerkat64_1h_128px.md"}
 
 
